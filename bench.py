@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the COLA hot path on GB300 (one JSON line on stdout).
+
+A "step" here is one pass of the whole hot path over one batch: Philox white noise -> 2LPT
+initial conditions -> the nsteps+1 force evaluations of eq. ALCtimestep (deposit, 3-D FFT,
+k-space Green's function, inverse FFTs, gather + COLA kick/drift) -> CIC density -> P(k).
+The metric is particle-updates per second: np^3 * nsteps / (wall time of one step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU (torchrun): every rank runs an independent realisation (different seed); there is no
+collective on the data path ("replicas only", weak scaling); value = sum over ranks / max time.
+--impl reference times the float64 CPU oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cola_256p_768g_L100"
+METRIC = "COLA particle-updates/s (N_p x steps / s), fwd and fwd+adjoint, on 1 GB300 vs plain GPU"
+UNIT = "particle-updates/s"
+NSTEPS = 10
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing ----------------------------------------------------------------
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region ------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.samples = []
+        self.window = None
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_id), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append((time.time(), parts))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        t0, t1 = self.window
+        sel = [p for (t, p) in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or [p for _, p in self.samples[-3:]]
+        if not sel:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[0]) for p in sel if num(p[0]) is not None]
+        mx = [num(p[1]) for p in sel if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in sel for i in range(4) if p[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sel)}
+
+
+# ---- roofline bookkeeping ------------------------------------------------------------------------
+def algorithmic_bytes(name, n_p, ng):
+    """Minimum bytes a launch of kernel `name` must move (float32 / complex64 / int32 data)."""
+    np3, ng3 = n_p**3, ng**3
+    if name.startswith("fft_"):
+        n = int(name.rsplit("_", 1)[1])
+        half = n * n * (n // 2 + 1) * 8
+        if name.startswith("fft_cols"):
+            return 2 * half          # in-place complex column pass: read + write
+        return half + n**3 * 4       # x pass: real rows <-> half-spectrum rows
+    table = {
+        "deposit_4x4": 16 * np3 + 4 * ng3,   # idx + s per particle, delta rows written once
+        "deposit_2x2": 16 * np3 + 4 * ng3,
+        "kspace_force": 4 * 8 * ng * ng * (ng // 2 + 1),
+        "gather_kick_drift": 72 * np3 + 12 * ng3,  # s, v, s1, s2 in, s, v out; 3 force meshes once
+        "keys": 16 * np3,
+        "scatter": 8 * np3,
+        "power_bin": 8 * ng * ng * (ng // 2 + 1),
+    }
+    return table.get(name)
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1301_0322_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(name, workload):
+    """dram read+write bytes per launch from a committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    rec = data.get(workload, {}).get(name)
+    if not rec or rec.get("source_digest") != kernel_source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---- the float64 oracle as a CPU baseline ------------------------------------------------------
+_ORACLE_STATE = {}
+
+
+def oracle_sample(workload):
+    """One COLA step (PM force at a_0, kick to a_1/2, drift to a_1) of the float64 oracle on a
+    periodic sub-volume of the workload at the same resolution: half the box side, half the
+    particles and mesh cells per side (1/8 of the particles and cells).  The 2LPT initial
+    conditions are set up once, untimed.  Returns (particle-updates/s, seconds, description)."""
+    import numpy as np
+
+    from oracle import cola as oc
+    from oracle import lpt
+    from oracle.cosmology import Cosmology, time_grid
+    from paper_1301_0322_gb300 import inputs
+
+    n_p, ng, box, seed = inputs.WORKLOADS[workload]
+    n_p, ng, box = n_p // 2, ng // 2, box / 2
+    if workload not in _ORACLE_STATE:
+        cosmo = Cosmology(**inputs.COSMOLOGY)
+        cfg = oc.ColaConfig(n_p=n_p, n_g=ng, box=box, cosmo=cosmo, nsteps=NSTEPS)
+        w = inputs.gaussian_noise(n_p, seed).reshape(n_p, n_p, n_p).astype(np.float64)
+        s1, s2 = lpt.ic_2lpt(w, box, cosmo)
+        a, mid = time_grid(cfg.a_init, cfg.a_final, NSTEPS)
+        g = cosmo.growth(a)
+        coef = (cosmo.kick_cola(a[0], mid[0], a[0], cfg.n_lpt), cosmo.drift_cola(a[0], a[1], mid[0], cfg.n_lpt))
+        _ORACLE_STATE[workload] = (cfg, s1, s2, a, g, coef)
+    cfg, s1, s2, a, g, (ck, cd) = _ORACLE_STATE[workload]
+    s = g["D1"][0] * s1 + g["D2"][0] * s2
+    v = np.zeros_like(s)
+    t0 = time.perf_counter()
+    acc = oc.acceleration(s, cfg, a[0])
+    v = v + ck * (acc - g["T2D1"][0] * s1 - g["T2D2"][0] * s2)
+    s = s + cd * v + (g["D1"][1] - g["D1"][0]) * s1 + (g["D2"][1] - g["D2"][0]) * s2
+    dt = time.perf_counter() - t0
+    desc = (f"one float64 oracle COLA step (PM force, kick, drift) on a {box:g} Mpc/h sub-volume at the "
+            f"workload's resolution ({n_p}^3 particles, {ng}^3 mesh, 1/8 of the workload)")
+    return n_p**3 / dt, dt, desc
+
+
+def reference_arm(args):
+    rank, world, _ = dist_setup("gloo")
+    if rank != 0:
+        barrier(world)
+        return
+    cores = os.cpu_count()
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, dt, desc = oracle_sample(args.workload)
+        if i >= args.warmup:
+            times.append(dt)
+    from paper_1301_0322_gb300 import inputs
+    n_p = inputs.WORKLOADS[args.workload][0]
+    per_step = statistics.mean(times)
+    value = (n_p // 2) ** 3 / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nsteps": NSTEPS, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+# ---- the GB300 arm ------------------------------------------------------------------------------------
+def gb300_arm(args):
+    import ctypes
+
+    import torch
+
+    import paper_1301_0322_gb300 as cola
+    from paper_1301_0322_gb300 import inputs
+
+    rank, world, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_p, ng, box, seed = inputs.WORKLOADS[args.workload]
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=NSTEPS, device=dev, **inputs.COSMOLOGY)
+    h = plan.handle
+    lib = cola.load_library()
+    n3 = n_p**3
+    nbins = ng // 2
+    noise = plan._empty(n3)
+    s, v, s1, s2 = (plan._empty((3, n3)) for _ in range(4))
+    delta = plan._empty(ng**3)
+    k, pk = plan._empty(nbins, torch.float64), plan._empty(nbins, torch.float64)
+    nm = plan._empty(nbins, torch.int64)
+
+    def one_step(sd):
+        cola.cola_noise(h, sd, noise)
+        cola.cola_ic_2lpt(h, noise, s, v, s1, s2)
+        for i in range(NSTEPS + 1):
+            cola.cola_step(h, i, s, v, s1, s2)
+        cola.cola_density(h, s, None, delta)
+        cola.cola_power(h, delta, nbins, k, pk, nm)
+
+    base_seed = seed + 1000 * rank
+    gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+    gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    for i in range(args.warmup):
+        one_step(base_seed + i)
+    plan.status()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    cnt0 = ctypes.c_uint64()
+    lib.cola_launch_count(ctypes.byref(cnt0))
+    lib.cola_profile(h, 1)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        one_step(base_seed + 100 + i)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_wall1 = time.time()
+    torch.cuda.synchronize()
+    lib.cola_profile(h, 0)
+    cnt1 = ctypes.c_uint64()
+    lib.cola_launch_count(ctypes.byref(cnt1))
+    barrier(world)
+    plan.status()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    clocks = None
+    if sampler:
+        sampler.mark(t_wall0, t_wall1)
+        clocks = sampler.stop()
+    # per-kernel device time from the events recorded around every launch
+    nmax = 256
+    names = ctypes.create_string_buffer(64 * nmax)
+    launches = (ctypes.c_int64 * nmax)()
+    msk = (ctypes.c_double * nmax)()
+    count = ctypes.c_int32()
+    lib.cola_profile_read(h, nmax, names, launches, msk, ctypes.byref(count))
+    kernels = {}
+    for i in range(count.value):
+        nm_ = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        kernels[nm_] = {"launches": int(launches[i]), "ms": float(msk[i])}
+    total_ms = ms_step * args.steps
+    for kv in kernels.values():
+        kv["share"] = kv["ms"] / total_ms
+    dom = max(kernels, key=lambda x: kernels[x]["ms"])
+    alg = algorithmic_bytes(dom, n_p, ng)
+    avg_ms = kernels[dom]["ms"] / kernels[dom]["launches"]
+    peak, peak_kind = hbm_peak()
+    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": measured_traffic(dom, args.workload), "bytes_per_launch": alg,
+                "avg_launch_ms": avg_ms}
+    value = world * n3 * NSTEPS / (ms_step * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_noise = torch.empty(n3, dtype=torch.float32, pin_memory=True)
+        h_s = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
+        h_v = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
+        h_pk = torch.empty(nbins, dtype=torch.float64, pin_memory=True)
+        cola.cola_noise(h, base_seed, noise)
+        h_noise.copy_(noise)
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 5))
+
+        def e2e_step():
+            noise.copy_(h_noise, non_blocking=True)
+            cola.cola_ic_2lpt(h, noise, s, v, s1, s2)
+            for i in range(NSTEPS + 1):
+                cola.cola_step(h, i, s, v, s1, s2)
+            cola.cola_density(h, s, None, delta)
+            cola.cola_power(h, delta, nbins, k, pk, nm)
+            h_s.copy_(s, non_blocking=True)
+            h_v.copy_(v, non_blocking=True)
+            h_pk.copy_(pk, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, world, dev)
+        e2e = {"value": world * n3 * NSTEPS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": 4 * n3, "d2h_bytes_per_step": 2 * 12 * n3 + 8 * nbins}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        reps, vals, desc, spent = 0, [], "", 0.0
+        while spent < 10.0 and reps < 4:
+            val, dt, desc = oracle_sample(args.workload)
+            vals.append(val)
+            spent += dt
+            reps += 1
+        cpu = {"value": statistics.median(vals), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{desc}; median of {reps} repetitions"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": f"{n_p}^3", "mesh": f"{ng}^3", "box_mpc_h": box,
+                       "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations + density + P(k)",
+                       "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (meshes of several GB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(cnt1.value - cnt0.value),
+            "kernels": {kk: {"launches": kv["launches"], "ms_per_step": kv["ms"] / args.steps,
+                             "share": round(kv["share"], 4)} for kk, kv in
+                        sorted(kernels.items(), key=lambda x: -x[1]["ms"])},
+        }
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        reference_arm(a)
+    else:
+        gb300_arm(a)

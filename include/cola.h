@@ -1,0 +1,172 @@
+/*
+ * cola.h -- C ABI of the GB300 (sm_103a) COLA hot path.
+ *
+ * COLA (COmoving Lagrangian Acceleration; Tassev, Zaldarriaga & Eisenstein 2013,
+ * arXiv:1301.0322) evolves particles of a periodic box in the frame comoving with their
+ * second-order Lagrangian perturbation theory (2LPT) trajectories:
+ *     x = q + s,  s_res = s - D1 s1 - D2 s2                                   (App. A.3)
+ *     T^2[s_res] = -(3/2) Om a d_x d_x^-2 delta - T^2[D1] s1 - T^2[D2] s2      (eq. eomALC)
+ * with the modified Kick/Drift operators of eq. KDKALC (u(a) = a^nLPT) applied in the order
+ * of eq. ALCtimestep and the frame changes L-/L+ of eq. Lops.  The force is a particle-mesh
+ * (PM) force on a periodic mesh (Sec. 2).
+ *
+ * Conventions shared by every call
+ *  - Particles live on an np^3 Lagrangian lattice, q = L (ix, iy, iz) / np, particle index
+ *    p = (iz np + iy) np + ix.  Per-particle vectors are structure-of-arrays float32 [3][np^3]
+ *    (all x components, then y, then z).  Meshes are float32 or int64 [iz][iy][ix], ng^3.
+ *  - "s" is the displacement of eq. eom (x = q + s, positions taken modulo L); "v" is the
+ *    velocity T[s] (the residual velocity v_res between L- and L+, App. A.3).
+ *  - All array pointers are DEVICE pointers owned by the caller; the library never allocates
+ *    device memory.  It needs one caller-allocated workspace (cola_workspace_bytes,
+ *    cola_set_workspace) that holds its meshes, tables and sort buffers.
+ *  - Calls are asynchronous on the given CUDA stream (cola_stream = cudaStream_t; NULL = the
+ *    legacy default stream).  Host-side argument errors return immediately; errors found by a
+ *    kernel are latched in the workspace and reported by cola_status.
+ *  - Return codes: COLA_OK or one of the COLA_E* values below; cola_last_error() gives a
+ *    message for the calling thread.  No C++ exception crosses this boundary.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the caller (calls on
+ *    different plans with different workspaces are independent).
+ */
+#ifndef COLA_GB300_H
+#define COLA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COLA_OK 0
+#define COLA_EINVAL 1          /* bad argument (size, pointer, range)                      */
+#define COLA_ECUDA 2           /* a CUDA runtime call failed                               */
+#define COLA_EOVERFLOW 3       /* a device check failed (fixed-point overflow, non-finite) */
+#define COLA_EUNSUPPORTED 4    /* mesh or lattice size without an FFT kernel               */
+#define COLA_ENOWORKSPACE 5    /* cola_set_workspace has not been called                   */
+
+#define COLA_NCOEF 16 /* columns of the cola_coeffs table */
+
+typedef void* cola_stream; /* cudaStream_t */
+typedef struct cola_plan cola_plan;
+
+/* Background cosmology (flat or curved LCDM without radiation) and the linear spectrum. */
+typedef struct {
+  double omega_m;  /* matter density today (eq. eom: Om)                               */
+  double omega_l;  /* cosmological constant; curvature 1 - Om - OL enters H(a)         */
+  double h;        /* H0 / (100 km/s/Mpc), enters the BBKS shape Gamma = Om h          */
+  double sigma8;   /* rms linear density in 8 Mpc/h top hats at a = 1                  */
+  double n_s;      /* primordial spectral index                                        */
+} cola_cosmo;
+
+/* One simulation: lattice, mesh, box, cosmology and the time stepping of App. A.3. */
+typedef struct {
+  int64_t np;         /* particles per side; np^3 particles                                 */
+  int64_t ng;         /* PM mesh cells per side (Sec. 2 uses ng = 3 np)                       */
+  double box;         /* periodic box side L in Mpc/h                                         */
+  cola_cosmo cosmo;
+  double n_lpt;       /* u(a) = a^nLPT of eq. KDKALC; the paper uses -2.5 (App. A.3.2)        */
+  int32_t nsteps;     /* number of time steps, uniform in a (App. A.3.2)                      */
+  double a_init;      /* initial scale factor (z = 9 -> 0.1 in Sec. 2)                        */
+  double a_final;     /* final scale factor (1.0)                                            */
+  int32_t deconv;     /* CIC deconvolution power p in 1/W(k)^p of the force: 0, 1 (default), 2 */
+  int32_t fixed_bits; /* F: CIC positions are quantised to 2^-F cell (default 16, 8..20)      */
+} cola_config;
+
+/* Fill *cfg with the 32^3-particle / 64^3-mesh defaults (L = 100 Mpc/h, Om = 0.27, OL = 0.73,
+ * h = 0.7, sigma8 = 0.8, ns = 0.96, nLPT = -2.5, 10 steps from a = 0.1 to 1, deconv 1, F 16). */
+int cola_config_default(cola_config* cfg);
+
+/* Validate cfg and build a plan: float64 growth factors and step coefficients on the host
+ * (App. A.3), FFT twiddle tables.  np and ng must be in {32, 48, 64, 96, 128, 192, 256, 384,
+ * 512, 768, 1024, 1536, 2048} (COLA_EUNSUPPORTED otherwise), ng a multiple of 4.  Host memory
+ * only.  *out receives the plan; destroy it with cola_plan_destroy. */
+int cola_plan_create(const cola_config* cfg, cola_plan** out);
+int cola_plan_destroy(cola_plan* plan);
+
+/* Device workspace the plan needs, in bytes (meshes, sort bins, tables). */
+int cola_workspace_bytes(const cola_plan* plan, size_t* bytes);
+
+/* Hand the plan a device buffer of at least cola_workspace_bytes bytes, 256-byte aligned.
+ * The caller keeps ownership and must keep it alive while the plan is used.  The twiddle
+ * and coefficient tables are copied into it on `stream`. */
+int cola_set_workspace(cola_plan* plan, void* dev_ptr, size_t bytes, cola_stream stream);
+
+/* Host float64 table of the per-force-evaluation coefficients, (nsteps+1) rows x COLA_NCOEF:
+ *  0 a_i (force time)           1 (3/2) Om a_i             2 c_K = (u(kb)-u(ka))/T[u](a_i)
+ *  3 T^2[D1](a_i)               4 T^2[D2](a_i)             5 c_D = int_{a_i}^{a_i+1} u/Q da / u(a_i+1/2)
+ *  6 D1(a_i+1)-D1(a_i)          7 D2(a_i+1)-D2(a_i)        8 T[D1](a_i)
+ *  9 T[D2](a_i)                10 D1(a_i)                 11 D2(a_i)
+ * 12 ka (kick start)           13 kb (kick end)           14 a_i+1 (0 on the last row)
+ * 15 D2u(1), the 2LPT normalisation s2 = D2u(1) psi2.
+ * Row i merges K(a_i-1/2, a_i; a_i) K(a_i, a_i+1/2; a_i) of eq. ALCtimestep (ka = a_0 on the
+ * first row, kb = a_n on the last); rows i < nsteps also carry D(a_i, a_i+1; a_i+1/2).
+ * table must hold (nsteps+1)*COLA_NCOEF doubles. */
+int cola_coeffs(const cola_plan* plan, double* table);
+
+/* Unit-variance Gaussian white noise on the np^3 lattice: Philox4x32-10 (Salmon et al. 2011)
+ * with key = seed, counter block = cell / 4, Box-Muller on ((r >> 8) + 1) 2^-24 uniforms.
+ * noise: device float32 [np^3].  (The paper's initial conditions are Gaussian, Sec. 2.) */
+int cola_noise(cola_plan* plan, uint64_t seed, float* noise, cola_stream stream);
+
+/* 2LPT initial conditions at a_init (Sec. 2; App. A.3):
+ *   delta_k = w_k sqrt(P(k) np^3 / L^3) (BBKS P normalised to sigma8, k = 0 removed),
+ *   s1 = i k delta_k / k^2, s2 = D2u(1) * (-i k mu2_k / k^2) with
+ *   mu2 = sum_{i<j} (s1_i,i s1_j,j - s1_i,j^2), derivatives zero on their Nyquist plane;
+ *   s = D1(a_init) s1 + D2(a_init) s2 and v = 0 (the 2LPT velocity after L-(a_init), eq. Lops).
+ * noise: device float32 [np^3] (read only).  s, v, s1, s2: device float32 [3][np^3] outputs. */
+int cola_ic_2lpt(cola_plan* plan, const float* noise, float* s, float* v, float* s1, float* s2,
+                 cola_stream stream);
+
+/* Force evaluation `step` (0..nsteps) of eq. ALCtimestep at a_step, in place on (s, v):
+ * PM force at the current positions, Kick from ka to kb with a_c = a_step, then (step < nsteps)
+ * Drift from a_step to a_step+1 with a_c = a_step+1/2 (eq. KDKALC), or (step == nsteps) L+.
+ * s, v: device float32 [3][np^3], read and written; s1, s2: device float32 [3][np^3]. */
+int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1, const float* s2,
+              cola_stream stream);
+
+/* The unit PM force g = -d_x d_x^-2 delta at the particles (eq. eom without (3/2) Om a),
+ * CIC deposit -> FFT -> i k_j / (k^2 W^p) -> inverse FFT -> CIC gather.
+ * s: device float32 [3][np^3]; g: device float32 [3][np^3] output. */
+int cola_force(cola_plan* plan, const float* s, float* g, cola_stream stream);
+
+/* CIC density of the particles at displacements s (Sec. 3.1 analysis; the deposit of the
+ * force).  rho_fix (may be NULL): device int64 [ng^3], sum of integer CIC weights with
+ * positions quantised to 2^-F cell (sum = np^3 2^3F exactly); delta (may be NULL): device
+ * float32 [ng^3], rho_fix ng^3 / (np^3 2^3F) - 1. */
+int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta, cola_stream stream);
+
+/* Shell-averaged power spectrum of a density mesh (Sec. 3.1): P = (L^3/ng^6) |delta_k|^2 /
+ * W(k)^2 averaged over shells (b - 1/2) k_F <= |k| < (b + 1/2) k_F, b = 1..nbins.
+ * delta: device float32 [ng^3] (read only); k, pk: device float64 [nbins]; nmodes: device
+ * int64 [nbins].  nbins <= ng. */
+int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, double* pk,
+               int64_t* nmodes, cola_stream stream);
+
+/* Forward 3-D real-to-complex DFT (exp(-i k.x), unscaled) of a real mesh of side n, where
+ * n is the plan's ng (which = 0) or np (which = 1).  in: device float32 [n^3]; out: device
+ * complex64 [n][n][n/2+1] (interleaved re, im). */
+int cola_fft_r2c(cola_plan* plan, int32_t which, const float* in, float* out, cola_stream stream);
+
+/* Synchronise `stream` and report errors latched by kernels since the last call
+ * (COLA_EOVERFLOW for a fixed-point overflow or a non-finite position), then clear them. */
+int cola_status(cola_plan* plan, cola_stream stream);
+
+/* Measurement hooks (not part of the method).  cola_profile(plan, 1) makes every kernel the
+ * plan's calls launch record a CUDA event pair on the launching stream; cola_profile_read
+ * synchronises those events and returns, per kernel name (NUL-terminated, 64 bytes each in
+ * `names`), the launch count and total milliseconds, then clears the records.  At most
+ * max_entries kernels are returned; *count receives how many. */
+int cola_profile(cola_plan* plan, int32_t enable);
+int cola_profile_read(cola_plan* plan, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                      int32_t* count);
+
+/* Process-wide number of kernels this library has launched (all plans, all threads). */
+int cola_launch_count(uint64_t* count);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* cola_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLA_GB300_H */

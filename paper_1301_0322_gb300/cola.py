@@ -1,0 +1,260 @@
+"""Thin Python binding of the COLA C ABI (include/cola.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+libcola_gb300.so.  PyTorch supplies device memory (the workspace and the particle / mesh
+tensors) and the current CUDA stream.  The functions named ``cola_*`` mirror the C entry
+points one to one; ``Plan`` bundles a plan handle with its workspace.
+
+If the library has not been built, importing works but the first call raises ImportError
+(there is no fallback implementation).
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcola_gb300.so")
+
+COLA_OK = 0
+COLA_NCOEF = 16
+ERRORS = {1: "COLA_EINVAL", 2: "COLA_ECUDA", 3: "COLA_EOVERFLOW", 4: "COLA_EUNSUPPORTED", 5: "COLA_ENOWORKSPACE"}
+
+
+class ColaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class cola_cosmo(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double), ("h", ctypes.c_double),
+                ("sigma8", ctypes.c_double), ("n_s", ctypes.c_double)]
+
+
+class cola_config(ctypes.Structure):
+    _fields_ = [("np", ctypes.c_int64), ("ng", ctypes.c_int64), ("box", ctypes.c_double),
+                ("cosmo", cola_cosmo), ("n_lpt", ctypes.c_double), ("nsteps", ctypes.c_int32),
+                ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("deconv", ctypes.c_int32),
+                ("fixed_bits", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "cola_config_default": [ctypes.POINTER(cola_config)],
+    "cola_plan_create": [ctypes.POINTER(cola_config), ctypes.POINTER(_P)],
+    "cola_plan_destroy": [_P],
+    "cola_workspace_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "cola_set_workspace": [_P, _P, ctypes.c_size_t, _P],
+    "cola_coeffs": [_P, _P],
+    "cola_noise": [_P, ctypes.c_uint64, _P, _P],
+    "cola_ic_2lpt": [_P, _P, _P, _P, _P, _P, _P],
+    "cola_step": [_P, ctypes.c_int32, _P, _P, _P, _P, _P],
+    "cola_force": [_P, _P, _P, _P],
+    "cola_density": [_P, _P, _P, _P, _P],
+    "cola_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
+    "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
+    "cola_status": [_P, _P],
+    "cola_profile": [_P, ctypes.c_int32],
+    "cola_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
+    "cola_launch_count": [_P],
+    "cola_last_error": [],
+}
+_lib = None
+
+
+def load_library():
+    """Load libcola_gb300.so (raises ImportError if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1301_0322_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "cola_last_error" else ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _check(code):
+    if code != COLA_OK:
+        raise ColaError(code, load_library().cola_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to the COLA library must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _expect(t, dtype, numel, name):
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or t.numel() != numel or not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA {dtype} tensor with {numel} elements")
+
+
+# ---- one-to-one wrappers of the C entry points ---------------------------------------------
+def cola_config_default():
+    cfg = cola_config()
+    _check(load_library().cola_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def cola_plan_create(cfg):
+    h = ctypes.c_void_p()
+    _check(load_library().cola_plan_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def cola_plan_destroy(h):
+    _check(load_library().cola_plan_destroy(h))
+
+
+def cola_workspace_bytes(h):
+    n = ctypes.c_size_t()
+    _check(load_library().cola_workspace_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def cola_set_workspace(h, ws, stream=None):
+    _check(load_library().cola_set_workspace(h, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def cola_coeffs(h, nsteps):
+    out = np.zeros((nsteps + 1, COLA_NCOEF), dtype=np.float64)
+    _check(load_library().cola_coeffs(h, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def cola_noise(h, seed, noise, stream=None):
+    _check(load_library().cola_noise(h, ctypes.c_uint64(seed), _ptr(noise), _stream(stream)))
+
+
+def cola_ic_2lpt(h, noise, s, v, s1, s2, stream=None):
+    _check(load_library().cola_ic_2lpt(h, _ptr(noise), _ptr(s), _ptr(v), _ptr(s1), _ptr(s2), _stream(stream)))
+
+
+def cola_step(h, step, s, v, s1, s2, stream=None):
+    _check(load_library().cola_step(h, int(step), _ptr(s), _ptr(v), _ptr(s1), _ptr(s2), _stream(stream)))
+
+
+def cola_force(h, s, g, stream=None):
+    _check(load_library().cola_force(h, _ptr(s), _ptr(g), _stream(stream)))
+
+
+def cola_density(h, s, rho_fix, delta, stream=None):
+    _check(load_library().cola_density(h, _ptr(s), _ptr(rho_fix), _ptr(delta), _stream(stream)))
+
+
+def cola_power(h, delta, nbins, k, pk, nmodes, stream=None):
+    _check(load_library().cola_power(h, _ptr(delta), int(nbins), _ptr(k), _ptr(pk), _ptr(nmodes), _stream(stream)))
+
+
+def cola_fft_r2c(h, which, x, out, stream=None):
+    _check(load_library().cola_fft_r2c(h, int(which), _ptr(x), _ptr(out), _stream(stream)))
+
+
+def cola_status(h, stream=None):
+    _check(load_library().cola_status(h, _stream(stream)))
+
+
+# ---- convenience wrapper ----------------------------------------------------------------------
+class Plan:
+    """A COLA plan plus its device workspace (allocated with torch on ``device``)."""
+
+    def __init__(self, np_side=32, ng=64, box=100.0, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96,
+                 n_lpt=-2.5, nsteps=10, a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, device="cuda"):
+        cfg = cola_config_default()
+        cfg.np, cfg.ng, cfg.box = int(np_side), int(ng), float(box)
+        cfg.cosmo = cola_cosmo(omega_m, omega_l, h, sigma8, n_s)
+        cfg.n_lpt, cfg.nsteps, cfg.a_init, cfg.a_final = float(n_lpt), int(nsteps), float(a_init), float(a_final)
+        cfg.deconv, cfg.fixed_bits = int(deconv), int(fixed_bits)
+        self.cfg = cfg
+        self.np, self.ng, self.nsteps = int(np_side), int(ng), int(nsteps)
+        self.n3 = self.np**3
+        self.device = torch.device(device)
+        self.handle = cola_plan_create(cfg)
+        nbytes = cola_workspace_bytes(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_view = self.workspace[off:off + nbytes]
+        cola_set_workspace(self.handle, self._ws_view)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.cola_plan_destroy(h)
+            self.handle = None
+
+    def _empty(self, shape, dtype=torch.float32):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def coeffs(self):
+        return cola_coeffs(self.handle, self.nsteps)
+
+    def noise(self, seed, out=None):
+        out = self._empty(self.n3) if out is None else out
+        _expect(out, torch.float32, self.n3, "noise")
+        cola_noise(self.handle, seed, out)
+        return out
+
+    def ic_2lpt(self, noise):
+        _expect(noise, torch.float32, self.n3, "noise")
+        s, v, s1, s2 = (self._empty((3, self.n3)) for _ in range(4))
+        cola_ic_2lpt(self.handle, noise, s, v, s1, s2)
+        return s, v, s1, s2
+
+    def step(self, i, s, v, s1, s2):
+        for t, n in ((s, "s"), (v, "v"), (s1, "s1"), (s2, "s2")):
+            _expect(t, torch.float32, 3 * self.n3, n)
+        cola_step(self.handle, i, s, v, s1, s2)
+
+    def run(self, noise):
+        """2LPT initial conditions, then the nsteps+1 force evaluations of eq. ALCtimestep."""
+        s, v, s1, s2 = self.ic_2lpt(noise)
+        for i in range(self.nsteps + 1):
+            self.step(i, s, v, s1, s2)
+        return s, v, s1, s2
+
+    def force(self, s):
+        _expect(s, torch.float32, 3 * self.n3, "s")
+        g = self._empty((3, self.n3))
+        cola_force(self.handle, s, g)
+        return g
+
+    def density(self, s, rho=True, delta=True):
+        _expect(s, torch.float32, 3 * self.n3, "s")
+        ng3 = self.ng**3
+        r = self._empty(ng3, torch.int64) if rho else None
+        d = self._empty(ng3) if delta else None
+        cola_density(self.handle, s, r, d)
+        return r, d
+
+    def power(self, delta, nbins):
+        _expect(delta, torch.float32, self.ng**3, "delta")
+        k = self._empty(nbins, torch.float64)
+        pk = self._empty(nbins, torch.float64)
+        nm = self._empty(nbins, torch.int64)
+        cola_power(self.handle, delta, nbins, k, pk, nm)
+        return k, pk, nm
+
+    def fft_r2c(self, x, which=0):
+        n = self.ng if which == 0 else self.np
+        _expect(x, torch.float32, n**3, "x")
+        out = self._empty((n, n, n // 2 + 1), torch.complex64)
+        cola_fft_r2c(self.handle, which, x, out)
+        return out
+
+    def status(self):
+        cola_status(self.handle)

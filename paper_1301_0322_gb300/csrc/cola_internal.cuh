@@ -1,0 +1,154 @@
+// Internal declarations shared by the CUDA translation units of the COLA library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cola.h"
+#include "profiler.cuh"
+
+namespace cola {
+
+// error bits latched in the workspace by kernels
+enum : int { kErrOverflow = 1, kErrNonFinite = 2 };
+
+// per-step float32 coefficients on the device (row of kCoef32 floats per force evaluation)
+enum Coef32 : int {
+  kCKF = 0,   // c_K * (3/2) Om a_i     (multiplies the unit force g)
+  kCK1 = 1,   // c_K * T^2[D1](a_i)
+  kCK2 = 2,   // c_K * T^2[D2](a_i)
+  kCD = 3,    // drift coefficient
+  kDD1 = 4,   // D1(a_i+1) - D1(a_i)
+  kDD2 = 5,   // D2(a_i+1) - D2(a_i)
+  kTD1 = 6,   // T[D1](a_i)  (used by L+ on the last row)
+  kTD2 = 7,   // T[D2](a_i)
+  kLast = 8,  // 1 on the last row
+  kCoef32 = 16
+};
+
+// Fixed-point CIC geometry shared by the deposit, the gather and the binning:
+//   f_d = (floor(i_d ng 2^F / np) + floor(fl32(s_d * fl32(ng/L)) * 2^F)) mod (ng 2^F)
+struct Geometry {
+  int np, ng;
+  int64_t np3;
+  int fbits;
+  int ratio;      // ng / np when ng is a multiple of np, else 0
+  float scale32;  // fl32(ng / L)
+};
+
+struct Tiles {
+  int ty, tz;     // rows per tile along y and z (the tile spans the whole x row)
+  int nty, ntz;   // tiles per axis
+  int nbins;      // nty * ntz * 4 (4 boundary regions per tile)
+};
+
+struct Workspace {
+  float2* tw_g = nullptr;   // exp(-2 pi i m / ng), m < ng
+  float2* tw_p = nullptr;   // exp(-2 pi i m / np), m < np
+  float* coef = nullptr;    // (nsteps+1) x kCoef32
+  int* err = nullptr;       // latched error bits
+  // PM step (aliases the IC region)
+  float2* meshA = nullptr;  // half spectrum, ng x ng x Pg
+  float2* meshG[3] = {nullptr, nullptr, nullptr};
+  float* freal = nullptr;   // 3 x ng^3 force meshes (freal[0..ng^3) doubles as delta)
+  // particle binning
+  int* keys = nullptr;
+  unsigned* idx = nullptr;
+  int* counts = nullptr;    // nbins
+  int* offsets = nullptr;   // nbins + 1
+  int* cursor = nullptr;    // nbins
+  // power spectrum accumulators: nbins_max x (k sum, p sum) doubles + counts
+  double* pk_acc = nullptr;
+  unsigned long long* pk_cnt = nullptr;
+  // initial conditions (alias the PM meshes)
+  float2* icC0 = nullptr;
+  float2* icC1 = nullptr;
+  float* icR[3] = {nullptr, nullptr, nullptr};
+};
+
+}  // namespace cola
+
+struct cola_plan {
+  cola_config cfg;
+  cola::Geometry geo;
+  cola::Tiles tiles;
+  int Pg = 0, Pp = 0;  // padded half-spectrum row lengths (complex) for ng and np
+  int64_t ng3 = 0;
+  std::vector<double> coef64;
+  std::vector<float> coef32;
+  std::vector<float2> tw_g, tw_p;
+  double pk_amp = 0.0;  // A of P(k) = A k^ns T^2(k)
+  double d2u1 = 0.0;
+  size_t ws_bytes = 0;
+  void* ws_base = nullptr;
+  cola::Workspace ws;
+  cola::Profiler prof;
+};
+
+namespace cola {
+
+// ---- host helpers (api.cu) ------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+bool fft_size_supported(int n);
+
+// ---- host coefficient module (coeffs.cpp) -----------------------------------------------
+struct HostCosmo;
+int build_coefficients(const cola_config& cfg, std::vector<double>& table, double& pk_amp, double& d2u1,
+                       std::string& why);
+void twiddle_table(int n, std::vector<float2>& out);
+
+// ---- launchers (kernels_*.cu) ------------------------------------------------------------
+// FFT passes (fft_kernels.cu)
+int launch_fft_x_r2c(int n, const float* in, float2* out, int64_t nrows, int P, const float2* tw, cudaStream_t st);
+int launch_fft_x_c2r(int n, const float2* in, float* out, int64_t nrows, int P, const float2* tw, float scale,
+                     cudaStream_t st);
+int launch_fft_cols(int n, bool inverse, float2* data, int64_t nslabs, int64_t slab_stride, int64_t row_stride,
+                    int ncols, const float2* tw, cudaStream_t st);
+// 3-D helpers built on the passes: r2c (x then y then z) and c2r (z, y, x), layout [n][n][P]
+int fft3d_r2c(int n, int P, const float* in, float2* out, const float2* tw, cudaStream_t st);
+int fft3d_c2r(int n, int P, float2* in_destroyed, float* out, const float2* tw, float scale, cudaStream_t st);
+
+// PM kernels (pm_kernels.cu)
+int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st);
+int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, cudaStream_t st);
+int launch_scatter(const Geometry& g, const int* keys, int* cursor, unsigned* idx, cudaStream_t st);
+int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
+                   int64_t* rho, float* delta, int* err, cudaStream_t st);
+int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
+                        cudaStream_t st);
+// mode 0: kick + drift, 1: kick + L+ (last force evaluation), 2: write the gathered unit force to gout
+int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, float* v, const float* s1,
+                             const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st);
+
+// IC kernels (ic_kernels.cu)
+int launch_noise(int np, uint64_t seed, float* out, cudaStream_t st);
+int launch_ic_filter(int np, int P, double box, double amp, double n_s, double omega_m, double h, float2* wk,
+                     cudaStream_t st);
+// out = factor(k) * in on the half spectrum; kind selects the operator (see ic_kernels.cu)
+int launch_kmul(int n, int P, double box, int kind, int i, int j, float scale, const float2* in, float2* out,
+                cudaStream_t st);
+int launch_source_2lpt(int64_t n3, const float* fxx, const float* fyy, const float* fzz, float* out_acc,
+                       cudaStream_t st);
+int launch_source_sub_sq(int64_t n3, const float* f, float* acc, cudaStream_t st);
+int launch_ic_assemble(int64_t n3, float d1, float d2, const float* s1, const float* s2, float* s, float* v,
+                       cudaStream_t st);
+
+// power spectrum and utilities (power_kernels.cu)
+int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* acc,
+                     unsigned long long* cnt, cudaStream_t st);
+int launch_power_finish(int nbins, const double* acc, const unsigned long long* cnt, double* k, double* pk,
+                        int64_t* nmodes, cudaStream_t st);
+int launch_unpad(int n, int P, const float2* in, float2* out, cudaStream_t st);
+
+}  // namespace cola
+
+#define COLA_CUDA_CHECK(expr)                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) return ::cola::fail(COLA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define COLA_LAUNCH_CHECK() COLA_CUDA_CHECK(cudaGetLastError())

@@ -1,0 +1,250 @@
+// Shared-memory Stockham FFT engine for the PM solver (sm_103a).
+//
+// One thread block transforms a batch of independent 1-D sequences of length N.  Each thread
+// owns E elements (E/R butterflies of radix R per stage); T = N/E threads cooperate on one
+// sequence.  The first stage reads its inputs straight from the caller (global memory or
+// shared memory), the last stage writes straight to the caller; intermediate stages exchange
+// through shared memory (Stockham autosort: output in natural order, no bit reversal).
+//
+// Conventions: forward = exp(-2 pi i n k / N), inverse = exp(+2 pi i n k / N), neither scaled.
+// Twiddles come from a float2 table tw[m] = exp(-2 pi i m / NT) computed in float64 on the
+// host; stage twiddles exp(-2 pi i m / N) are read at tw[m * TWS] with NT = N * TWS.
+#pragma once
+#include <cstdint>
+#include <utility>
+
+namespace cola {
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward sign) or +i (inverse sign)
+template <bool INV>
+__device__ __forceinline__ float2 c_rot(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Compile-time sine/cosine (Taylor series in double; arguments in [0, 2 pi)) for the constant
+// twiddles inside the small in-register DFTs.
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double cx_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 40; ++n) {
+    term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double cx_sin(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n < 40; ++n) {
+    term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+
+template <int R, int K, bool INV>
+struct ConstTw {
+  static constexpr float re = (float)cx_cos(2.0 * kPi * K / R);
+  static constexpr float im = (INV ? 1.0f : -1.0f) * (float)cx_sin(2.0 * kPi * K / R);
+};
+
+// y <- x * exp(-+2 pi i K / R), with the trivial angles special-cased
+template <int R, int K, bool INV>
+__device__ __forceinline__ float2 mul_const_tw(float2 x) {
+  if constexpr (K == 0) {
+    return x;
+  } else if constexpr (4 * K == R) {
+    return c_rot<INV>(x);
+  } else {
+    return c_mul(x, make_float2(ConstTw<R, K, INV>::re, ConstTw<R, K, INV>::im));
+  }
+}
+
+// ---- small in-register DFTs -------------------------------------------------------------
+template <int R, bool INV>
+struct DFT;
+
+template <bool INV>
+struct DFT<2, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = c_add(a, b);
+    v[1] = c_sub(a, b);
+  }
+};
+
+template <bool INV>
+struct DFT<3, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    // omega = exp(-+2 pi i / 3) = -1/2 + i s,  s = -+sqrt(3)/2
+    constexpr float s = INV ? 0.866025403784438647f : -0.866025403784438647f;
+    const float2 t1 = c_add(v[1], v[2]);
+    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+    const float2 t3 = c_sub(v[1], v[2]);
+    v[0] = c_add(v[0], t1);
+    v[1] = make_float2(fmaf(-s, t3.y, t2.x), fmaf(s, t3.x, t2.y));
+    v[2] = make_float2(fmaf(s, t3.y, t2.x), fmaf(-s, t3.x, t2.y));
+  }
+};
+
+template <bool INV>
+struct DFT<4, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t0 = c_add(v[0], v[2]), t1 = c_sub(v[0], v[2]);
+    const float2 t2 = c_add(v[1], v[3]), t3 = c_rot<INV>(c_sub(v[1], v[3]));
+    v[0] = c_add(t0, t2);
+    v[2] = c_sub(t0, t2);
+    v[1] = c_add(t1, t3);
+    v[3] = c_sub(t1, t3);
+  }
+};
+
+// Even composite radices R = 2H (6, 8, 12, 16): one radix-2 decimation-in-time split.
+template <int R, bool INV>
+struct DFT {
+  static_assert(R % 2 == 0 && R <= 16, "unsupported radix");
+  static constexpr int H = R / 2;
+  template <int... K>
+  __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o,
+                                                 std::integer_sequence<int, K...>) {
+    ((v[K] = c_add(e[K], mul_const_tw<R, K, INV>(o[K])), v[K + H] = c_sub(e[K], mul_const_tw<R, K, INV>(o[K]))), ...);
+  }
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 e[H], o[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    DFT<H, INV>::run(e);
+    DFT<H, INV>::run(o);
+    combine(v, e, o, std::make_integer_sequence<int, H>{});
+  }
+};
+
+// ---- size table: radix list (product N) and elements per thread E --------------------------
+template <int... Rs>
+struct Radices {};
+
+template <int N>
+struct FFTConf;
+#define COLA_FFT_CONF(N_, E_, ...)            \
+  template <>                                 \
+  struct FFTConf<N_> {                        \
+    static constexpr int N = N_;              \
+    static constexpr int E = E_;              \
+    static constexpr int T = N_ / E_;         \
+    using radices = Radices<__VA_ARGS__>;     \
+  };
+COLA_FFT_CONF(16, 16, 16)
+COLA_FFT_CONF(24, 24, 8, 3)
+COLA_FFT_CONF(32, 8, 8, 4)
+COLA_FFT_CONF(48, 12, 4, 4, 3)
+COLA_FFT_CONF(64, 8, 8, 8)
+COLA_FFT_CONF(96, 24, 8, 12)
+COLA_FFT_CONF(128, 16, 16, 8)
+COLA_FFT_CONF(192, 24, 8, 8, 3)
+COLA_FFT_CONF(256, 16, 16, 16)
+COLA_FFT_CONF(384, 24, 8, 8, 6)
+COLA_FFT_CONF(512, 8, 8, 8, 8)
+COLA_FFT_CONF(768, 24, 8, 8, 12)
+COLA_FFT_CONF(1024, 16, 16, 16, 4)
+COLA_FFT_CONF(1536, 24, 8, 8, 8, 3)
+COLA_FFT_CONF(2048, 16, 16, 16, 8)
+#undef COLA_FFT_CONF
+
+template <class L>
+struct FirstRadix;
+template <int R0, int... Rs>
+struct FirstRadix<Radices<R0, Rs...>> {
+  static constexpr int value = R0;
+};
+
+// ---- Stockham stages --------------------------------------------------------------------
+template <int N, int E, int TWS, bool INV>
+struct Stockham {
+  static constexpr int T = N / E;
+
+  // twiddle and in-register DFT of every butterfly this thread owns (butterfly j = t + T q,
+  // inputs v[q R + r] = x[j + r N/R]), for a stage of radix R after NS points were combined
+  template <int R, int NS>
+  __device__ __forceinline__ static void compute(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+#pragma unroll
+    for (int q = 0; q < E / R; ++q) {
+      if constexpr (NS > 1) {
+        const int jj = (t + T * q) % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const int e = jj * r * (N / (NS * R));
+          float2 w = __ldg(tw + e * TWS);
+          if (INV) w.y = -w.y;
+          v[q * R + r] = c_mul(v[q * R + r], w);
+        }
+      }
+      DFT<R, INV>::run(&v[q * R]);
+    }
+  }
+
+  template <int R, int NS>
+  __device__ __forceinline__ static int out_index(int j, int r) {
+    return (j / NS) * NS * R + (j % NS) + r * NS;
+  }
+
+  // Run the stages NS.. of the radix list.  v holds the inputs of the first listed stage.
+  // mem(n) -> float2& : exchange buffer slot for element n of this thread's sequence.
+  // store(n, x)       : final output of element n.
+  template <int NS, int R, int... Rest, class Mem, class Store>
+  __device__ __forceinline__ static void run(float2 (&v)[E], int t, const float2* __restrict__ tw,
+                                             Mem& mem, Store& store) {
+    compute<R, NS>(v, t, tw);
+    if constexpr (sizeof...(Rest) == 0) {
+      static_assert(NS * R == N, "radix list does not multiply to N");
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < E / R; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) store(out_index<R, NS>(t + T * q, r), v[q * R + r]);
+    } else {
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < E / R; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) mem(out_index<R, NS>(t + T * q, r)) = v[q * R + r];
+      __syncthreads();
+      constexpr int R2 = FirstRadix<Radices<Rest...>>::value;
+#pragma unroll
+      for (int q = 0; q < E / R2; ++q)
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[q * R2 + r] = mem(t + T * q + r * (N / R2));
+      run<NS * R, Rest...>(v, t, tw, mem, store);
+    }
+  }
+
+  template <int... Rs, class Mem, class Store>
+  __device__ __forceinline__ static void run_all(Radices<Rs...>, float2 (&v)[E], int t,
+                                                 const float2* __restrict__ tw, Mem& mem, Store& store) {
+    run<1, Rs...>(v, t, tw, mem, store);
+  }
+};
+
+// Convenience wrapper: load the first-stage inputs with load(n) and run the whole transform.
+template <int N, int TWS, bool INV, class Load, class Mem, class Store>
+__device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Load& load, Mem& mem, Store& store) {
+  using C = FFTConf<N>;
+  constexpr int E = C::E, T = C::T;
+  constexpr int R0 = FirstRadix<typename C::radices>::value;
+  float2 v[E];
+#pragma unroll
+  for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[q * R0 + r] = load(t + T * q + r * (N / R0));
+  Stockham<N, E, TWS, INV>::run_all(typename C::radices{}, v, t, tw, mem, store);
+}
+
+}  // namespace cola

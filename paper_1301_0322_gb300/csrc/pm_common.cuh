@@ -1,0 +1,46 @@
+// Device helpers shared by the particle-mesh kernels: the fixed-point CIC coordinates.
+#pragma once
+#include "cola_internal.cuh"
+
+namespace cola {
+
+// Lattice index of particle p = (iz np + iy) np + ix.
+__device__ __forceinline__ void lattice_index(const Geometry& g, int64_t p, int& ix, int& iy, int& iz) {
+  if (g.np3 <= 0xFFFFFFFFLL) {
+    const unsigned pu = (unsigned)p, n = (unsigned)g.np;
+    const unsigned r = pu / n;
+    ix = (int)(pu - r * n);
+    iz = (int)(r / n);
+    iy = (int)(r - (unsigned)iz * n);
+  } else {
+    const int64_t r = p / g.np;
+    ix = (int)(p - r * g.np);
+    iz = (int)(r / g.np);
+    iy = (int)(r - (int64_t)iz * g.np);
+  }
+}
+
+// Fixed-point coordinate of one axis (the library's CIC quantisation, shared bit for bit
+// with the deposit test oracle):
+//   f = (floor(i ng 2^F / np) + floor(fl32(s * fl32(ng/L)) * 2^F)) mod (ng 2^F)
+// returns the cell (f >> F) and the upper-neighbour weight t = f mod 2^F.
+__device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, int& cell, int& t) {
+  const int64_t one = 1LL << g.fbits;
+  const int64_t period = (int64_t)g.ng << g.fbits;
+  const int64_t q = g.ratio ? ((int64_t)i * g.ratio) << g.fbits : (((int64_t)i * g.ng) << g.fbits) / g.np;
+  const float w = __fmul_rn(s, g.scale32);
+  const float ws = __fmul_rn(w, (float)one);  // exact: power-of-two scaling
+  int64_t f = q + (int64_t)floorf(ws);
+  if (f < 0) f += period;
+  if (f >= period) f -= period;
+  if (f < 0 || f >= period) {  // displacement beyond one box length
+    f %= period;
+    if (f < 0) f += period;
+  }
+  cell = (int)(f >> g.fbits);
+  t = (int)(f & (one - 1));
+}
+
+__device__ __forceinline__ int wrap_inc(int c, int n) { return c + 1 == n ? 0 : c + 1; }
+
+}  // namespace cola

@@ -1,0 +1,349 @@
+// Particle-mesh kernels of a COLA force evaluation (Sec. 2 PM code; App. A.1 eq. eom;
+// App. A.3 eq. KDKALC):
+//   binning  : particles -> (y, z) row tiles of the mesh (counting sort, integer atomics)
+//   deposit  : CIC mass of every particle touching a tile, int64 fixed point in shared memory
+//              (integer sums: the result does not depend on the order of the atomics)
+//   k-space  : g_j = i k_j delta_k / (k^2 W^p) / ng^3 (Nyquist plane of j and k = 0 set to 0)
+//   gather   : CIC interpolation of g with the deposit's weights, fused with the COLA Kick and
+//              Drift (or the final L+ of eq. Lops)
+#include "cola_internal.cuh"
+#include "pm_common.cuh"
+
+namespace cola {
+
+// ---- binning -------------------------------------------------------------------------------
+// key = ((tz_tile * nty) + ty_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
+// is the last row of its tile along y (z): its cloud also reaches the next tile.
+__device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
+  const int ty = cy / tl.ty, tz = cz / tl.tz;
+  const int ry = (cy - ty * tl.ty == tl.ty - 1) ? 1 : 0;
+  const int rz = (cz - tz * tl.tz == tl.tz - 1) ? 2 : 0;
+  return (tz * tl.nty + ty) * 4 + ry + rz;
+}
+
+__global__ void k_keys(Geometry g, Tiles tl, const float* __restrict__ s, int* __restrict__ keys,
+                       int* __restrict__ counts, int* __restrict__ err) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < g.np3;
+  int key = -1;
+  if (live) {
+    int ix, iy, iz;
+    lattice_index(g, p, ix, iy, iz);
+    const float sy = s[g.np3 + p], sz = s[2 * g.np3 + p];
+    if (!isfinite(s[p]) || !isfinite(sy) || !isfinite(sz)) atomicOr(err, kErrNonFinite);
+    int cy, ty, cz, tz;
+    fixed_axis(g, iy, sy, cy, ty);
+    fixed_axis(g, iz, sz, cz, tz);
+    key = tile_key(tl, cy, cz);
+    keys[p] = key;
+  }
+  // one atomic per distinct key in the warp
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+}
+
+// Exclusive scan of the bin counts (single block); resets the counts for the next use.
+__global__ void __launch_bounds__(1024) k_scan(int n, int* __restrict__ counts, int* __restrict__ offsets,
+                                               int* __restrict__ cursor) {
+  __shared__ int warp_sums[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(n, tid * chunk), b1 = min(n, b0 + chunk);
+  int local = 0;
+  for (int b = b0; b < b1; ++b) local += counts[b];
+  int incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += y;
+    }
+    warp_sums[lane] = ws;  // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  for (int b = b0; b < b1; ++b) {
+    const int c = counts[b];
+    offsets[b] = run;
+    cursor[b] = run;
+    counts[b] = 0;
+    run += c;
+  }
+  if (tid == blockDim.x - 1) offsets[n] = warp_sums[(blockDim.x >> 5) - 1];
+}
+
+__global__ void k_scatter(int64_t np3, const int* __restrict__ keys, int* __restrict__ cursor,
+                          unsigned* __restrict__ idx) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < np3;
+  const int key = live ? keys[p] : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (live) idx[base + rank] = (unsigned)p;
+}
+
+// ---- deposit ----------------------------------------------------------------------------------
+// One block per tile of TY x TZ mesh rows (whole x extent).  It reads the particles binned to
+// the tile and the boundary regions of its three lower neighbours, accumulates exact int64
+// CIC weights in shared memory and writes the rows once (int64 and/or float overdensity).
+template <int TY, int TZ>
+__global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const float* __restrict__ s,
+                                                 const unsigned* __restrict__ idx, const int* __restrict__ offsets,
+                                                 int64_t* __restrict__ rho, float* __restrict__ delta,
+                                                 float dscale, int* __restrict__ err) {
+  extern __shared__ unsigned long long acc[];
+  __shared__ int rbeg[9], rpre[10];
+  const int ng = g.ng;
+  const int tyi = blockIdx.x % tl.nty, tzi = blockIdx.x / tl.nty;
+  const int y0 = tyi * TY, z0 = tzi * TZ;
+  const int ncell = TZ * TY * ng;
+  for (int i = threadIdx.x; i < ncell; i += blockDim.x) acc[i] = 0ull;
+  if (threadIdx.x == 0) {
+    const int tym = tyi == 0 ? tl.nty - 1 : tyi - 1;
+    const int tzm = tzi == 0 ? tl.ntz - 1 : tzi - 1;
+    const int tys[9] = {tyi, tyi, tyi, tyi, tym, tym, tyi, tyi, tym};
+    const int tzs[9] = {tzi, tzi, tzi, tzi, tzi, tzi, tzm, tzm, tzm};
+    const int reg[9] = {0, 1, 2, 3, 1, 3, 2, 3, 3};
+    int run = 0;
+    for (int k = 0; k < 9; ++k) {
+      const int b = (tzs[k] * tl.nty + tys[k]) * 4 + reg[k];
+      rbeg[k] = offsets[b];
+      rpre[k] = run;
+      run += offsets[b + 1] - offsets[b];
+    }
+    rpre[9] = run;
+  }
+  __syncthreads();
+  const int total = rpre[9];
+  const unsigned long long one = 1ull << g.fbits;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
+    const int64_t p = idx[rbeg[r] + (i - rpre[r])];
+    int ix, iy, iz;
+    lattice_index(g, p, ix, iy, iz);
+    int cx, tx, cy, ty, cz, tz;
+    fixed_axis(g, ix, s[p], cx, tx);
+    fixed_axis(g, iy, s[g.np3 + p], cy, ty);
+    fixed_axis(g, iz, s[2 * g.np3 + p], cz, tz);
+    const int cx1 = wrap_inc(cx, ng);
+    const unsigned long long wx0 = one - tx, wx1 = tx;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+      const int z = dz ? wrap_inc(cz, ng) : cz;
+      const int lz = z - z0;
+      if (lz < 0 || lz >= TZ) continue;
+      const unsigned long long wz = dz ? (unsigned long long)tz : one - tz;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int y = dy ? wrap_inc(cy, ng) : cy;
+        const int ly = y - y0;
+        if (ly < 0 || ly >= TY) continue;
+        const unsigned long long wzy = wz * (dy ? (unsigned long long)ty : one - ty);
+        unsigned long long* row = acc + (lz * TY + ly) * ng;
+        atomicAdd(row + cx, wzy * wx0);
+        atomicAdd(row + cx1, wzy * wx1);
+      }
+    }
+  }
+  __syncthreads();
+  bool overflow = false;
+  for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+    const int lz = i / (TY * ng), rem = i - lz * (TY * ng);
+    const int ly = rem / ng, x = rem - ly * ng;
+    const int64_t gi = ((int64_t)(z0 + lz) * ng + (y0 + ly)) * ng + x;
+    const unsigned long long v = acc[i];
+    overflow |= (v >> 62) != 0ull;
+    if (rho) rho[gi] = (int64_t)v;
+    if (delta) delta[gi] = fmaf(__ull2float_rn(v), dscale, -1.0f);
+  }
+  if (overflow) atomicOr(err, kErrOverflow);
+}
+
+// ---- k-space force --------------------------------------------------------------------------
+__device__ __forceinline__ float sinc_pi(int n, int ng) {
+  if (n == 0) return 1.0f;
+  const float x = (float)n / (float)ng;
+  return sinpif(x) / (3.14159265358979323846f * x);
+}
+
+__global__ void k_kspace_force(int ng, int P, float kf, int deconv, float norm, const float2* __restrict__ dk,
+                               float2* __restrict__ gx, float2* __restrict__ gy, float2* __restrict__ gz) {
+  const int nh = ng / 2 + 1;
+  const int64_t total = (int64_t)ng * ng * nh;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nh);
+    const int64_t r = i / nh;
+    const int ky = (int)(r % ng), kz = (int)(r / ng);
+    const int nx = kx, ny = ky < ng / 2 ? ky : ky - ng, nz = kz < ng / 2 ? kz : kz - ng;
+    const int64_t o = r * P + kx;
+    const int m2 = nx * nx + ny * ny + nz * nz;
+    float2 out[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (m2 != 0) {
+      float green = norm / (kf * kf * (float)m2);
+      if (deconv) {
+        const float sx = sinc_pi(nx, ng), sy = sinc_pi(ny, ng), sz = sinc_pi(nz, ng);
+        const float w = (sx * sx) * (sy * sy) * (sz * sz);
+        green /= (deconv == 2 ? w * w : w);
+      }
+      const float2 d = dk[o];
+      const float2 val = make_float2(d.x * green, d.y * green);
+      const int half = ng / 2;
+      const float kx_ = (nx == half) ? 0.f : kf * nx;
+      const float ky_ = (ny == -half) ? 0.f : kf * ny;
+      const float kz_ = (nz == -half) ? 0.f : kf * nz;
+      // i k (a + i b) = k (-b + i a)
+      out[0] = make_float2(-kx_ * val.y, kx_ * val.x);
+      out[1] = make_float2(-ky_ * val.y, ky_ * val.x);
+      out[2] = make_float2(-kz_ * val.y, kz_ * val.x);
+    }
+    gx[o] = out[0];
+    gy[o] = out[1];
+    gz[o] = out[2];
+  }
+}
+
+// ---- gather + kick + drift -------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather_kick_drift(Geometry g, const float* __restrict__ fmesh,
+                                                            float* __restrict__ s, float* __restrict__ v,
+                                                            const float* __restrict__ s1, const float* __restrict__ s2,
+                                                            const float* __restrict__ coef, int mode,
+                                                            float* __restrict__ gout) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np3) return;
+  const int64_t n3 = g.np3;
+  const int ng = g.ng;
+  const int64_t ng3 = (int64_t)ng * ng * ng;
+  int ix, iy, iz;
+  lattice_index(g, p, ix, iy, iz);
+  const float sp[3] = {s[p], s[n3 + p], s[2 * n3 + p]};
+  int c[3], t[3];
+  fixed_axis(g, ix, sp[0], c[0], t[0]);
+  fixed_axis(g, iy, sp[1], c[1], t[1]);
+  fixed_axis(g, iz, sp[2], c[2], t[2]);
+  const float inv_one = 1.0f / (float)(1 << g.fbits);
+  float w1[3], w0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    w1[d] = (float)t[d] * inv_one;  // exact
+    w0[d] = 1.0f - w1[d];           // exact
+  }
+  const int xs[2] = {c[0], wrap_inc(c[0], ng)};
+  const int ys[2] = {c[1], wrap_inc(c[1], ng)};
+  const int zs[2] = {c[2], wrap_inc(c[2], ng)};
+  float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const float wzy = (dz ? w1[2] : w0[2]) * (dy ? w1[1] : w0[1]);
+      const int64_t row = ((int64_t)zs[dz] * ng + ys[dy]) * ng;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const float w = wzy * (dx ? w1[0] : w0[0]);
+        const int64_t gi = row + xs[dx];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f[j] = fmaf(w, __ldg(fmesh + j * ng3 + gi), f[j]);
+      }
+    }
+  if (mode == 2) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gout[j * n3 + p] = f[j];
+    return;
+  }
+  const float cKF = __ldg(coef + kCKF), cK1 = __ldg(coef + kCK1), cK2 = __ldg(coef + kCK2);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float a1 = s1[j * n3 + p], a2 = s2[j * n3 + p];
+    float vj = v[j * n3 + p];
+    vj += cKF * f[j] - cK1 * a1 - cK2 * a2;  // Kick (eq. KDKALC)
+    if (mode == 0) {
+      const float sj = sp[j] + __ldg(coef + kCD) * vj + __ldg(coef + kDD1) * a1 + __ldg(coef + kDD2) * a2;  // Drift
+      s[j * n3 + p] = sj;
+    } else {
+      vj += __ldg(coef + kTD1) * a1 + __ldg(coef + kTD2) * a2;  // L+ (eq. Lops)
+    }
+    v[j * n3 + p] = vj;
+  }
+}
+
+// ---- launchers ------------------------------------------------------------------------------------
+static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st) {
+  { LaunchScope ls_("keys", st);
+  k_keys<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, t, s, keys, counts, err); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, cudaStream_t st) {
+  { LaunchScope ls_("scan", st);
+  k_scan<<<1, 1024, 0, st>>>(t.nbins, counts, offsets, cursor); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_scatter(const Geometry& g, const int* keys, int* cursor, unsigned* idx, cudaStream_t st) {
+  { LaunchScope ls_("scatter", st);
+  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g.np3, keys, cursor, idx); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+template <int TY, int TZ>
+static int deposit_t(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
+                     int64_t* rho, float* delta, int* err, cudaStream_t st) {
+  const size_t smem = (size_t)TY * TZ * g.ng * sizeof(unsigned long long);
+  if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "deposit tile does not fit in shared memory");
+  if (smem > 48 * 1024)
+    COLA_CUDA_CHECK(cudaFuncSetAttribute(k_deposit<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double ng3 = (double)g.ng * g.ng * g.ng;
+  const float dscale = (float)(ng3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
+  { LaunchScope ls_(TY == 4 ? "deposit_4x4" : "deposit_2x2", st);
+  k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, s, idx, offsets, rho, delta, dscale, err); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
+                   int64_t* rho, float* delta, int* err, cudaStream_t st) {
+  if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, s, idx, offsets, rho, delta, err, st);
+  if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, s, idx, offsets, rho, delta, err, st);
+  return fail(COLA_EUNSUPPORTED, "deposit: unsupported tile shape");
+}
+
+int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
+                        cudaStream_t st) {
+  const float kf = (float)(2.0 * 3.14159265358979323846 / box);
+  const float norm = (float)(1.0 / ((double)ng * ng * ng));
+  const int64_t total = (int64_t)ng * ng * (ng / 2 + 1);
+  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(total, 256), 152 * 64);
+  { LaunchScope ls_("kspace_force", st);
+  k_kspace_force<<<blocks, 256, 0, st>>>(ng, P, kf, deconv, norm, dk, gx, gy, gz); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, float* v, const float* s1,
+                             const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st) {
+  { LaunchScope ls_("gather_kick_drift", st);
+  k_gather_kick_drift<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, s, v, s1, s2, coef_row, mode, gout); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+}  // namespace cola
