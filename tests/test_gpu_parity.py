@@ -96,7 +96,9 @@ def test_deposit_bit_exact(cola, case):
     rho, delta = plan.density(dev(s))
     rho = host(rho).reshape(ng, ng, ng)
     ref = omesh.cic_deposit_fixed(s, n_p, ng, box, 16)
-    assert rho.sum() == n_p**3 * 2**48
+    # exact total mass (the global sum can exceed int64, so add the high and low parts apart)
+    total = int((rho >> 24).sum()) * 2**24 + int((rho & (2**24 - 1)).sum())
+    assert total == n_p**3 * 2**48
     assert np.array_equal(rho, ref)
     d = host(delta).reshape(ng, ng, ng)
     dref = ref.astype(np.float64) * (ng**3 / (n_p**3 * 2.0**48)) - 1.0
