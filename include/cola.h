@@ -151,6 +151,25 @@ int cola_fft_r2c(cola_plan* plan, int32_t which, const float* in, float* out, co
  * (COLA_EOVERFLOW for a fixed-point overflow or a non-finite position), then clear them. */
 int cola_status(cola_plan* plan, cola_stream stream);
 
+/* cola_power without a plan, a workspace or any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate device memory
+ * themselves -- code hosted inside an application whose own pool allocator owns all device
+ * memory (where cudaMalloc/cudaFree are off limits and would synchronise the device), or a
+ * monitor attached to a running simulation that must not change its memory footprint.
+ * Same result as cola_power on a plan with this ng and box: P(k) of the float32 density
+ * delta [ng^3] in shells b = 1..nbins, written to the caller's device arrays k, pk (float64)
+ * and nmodes (int64).  Its scratch is one static device array sized for ng <= 128 (about
+ * 8.5 MiB held on every GPU that loads the library until the process exits); ng > 128 is
+ * rejected with COLA_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture on the device.  Every call shares the one
+ * array and leaves its contents behind (the shell accumulators are cleared at the start of
+ * each call), so calls that overlap on the GPU -- on different streams or from different
+ * threads -- race and must be serialised by the caller. */
+#define COLA_NOALLOC_MAX_NG 128
+int cola_power_noalloc(const float* delta, int32_t ng, double box, int32_t nbins, double* k, double* pk,
+                       int64_t* nmodes, cola_stream stream);
+
 /* Measurement hooks (not part of the method).  cola_profile(plan, 1) makes every kernel the
  * plan's calls launch record a CUDA event pair on the launching stream; cola_profile_read
  * synchronises those events and returns, per kernel name (NUL-terminated, 64 bytes each in

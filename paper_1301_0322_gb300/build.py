@@ -11,8 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcola_gb300.so")
-SOURCES = ["api.cu", "coeffs.cpp", "fft_kernels.cu", "pm_kernels.cu", "ic_kernels.cu", "power_kernels.cu"]
-HEADERS = ["cola_internal.cuh", "fft.cuh", "pm_common.cuh"]
+SOURCES = ["api.cu", "coeffs.cpp", "fft_kernels.cu", "pm_kernels.cu", "ic_kernels.cu", "power_kernels.cu",
+           "power_noalloc.cu"]
+HEADERS = ["cola_internal.cuh", "fft.cuh", "pm_common.cuh", "profiler.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "cola_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
     "cola_status": [_P, _P],
+    "cola_power_noalloc": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P],
     "cola_profile": [_P, ctypes.c_int32],
     "cola_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_launch_count": [_P],
@@ -159,6 +160,12 @@ def cola_density(h, s, rho_fix, delta, stream=None):
 
 def cola_power(h, delta, nbins, k, pk, nmodes, stream=None):
     _check(load_library().cola_power(h, _ptr(delta), int(nbins), _ptr(k), _ptr(pk), _ptr(nmodes), _stream(stream)))
+
+
+def cola_power_noalloc(delta, ng, box, nbins, k, pk, nmodes, stream=None):
+    """P(k) of a density mesh (ng <= 128) with no plan, workspace or device allocation."""
+    _check(load_library().cola_power_noalloc(_ptr(delta), int(ng), float(box), int(nbins), _ptr(k), _ptr(pk),
+                                             _ptr(nmodes), _stream(stream)))
 
 
 def cola_fft_r2c(h, which, x, out, stream=None):

@@ -1,0 +1,89 @@
+// cola_power_noalloc: the shell-averaged power spectrum of a small density mesh without any
+// plan, workspace or device allocation.
+//
+// Who needs it: code that measures P(k) from inside a host application that owns every byte
+// of device memory through its own pool allocator (so a library may not call cudaMalloc /
+// cudaFree behind its back, and those calls would also synchronise the whole device), and
+// monitoring tools attached to a running simulation that must not change its memory
+// footprint.  Such callers still pass their own input and output buffers.
+//
+// The scratch (the half spectrum, the shell accumulators and the twiddle table) lives in the
+// file-scope device array below, sized for meshes up to COLA_NOALLOC_MAX_NG^3.  Every GPU that
+// loads this library keeps that array (about 8.5 MiB) until the process exits.  Host code must
+// not pass the array's name to a kernel: on the host that name is only a stand-in for the
+// device symbol, so its device address is looked up once per device with
+// cudaGetSymbolAddress and that address is what the kernels receive.
+#include <mutex>
+#include <vector>
+
+#include "cola_internal.cuh"
+
+namespace cola {
+namespace {
+
+constexpr int kMaxNg = COLA_NOALLOC_MAX_NG;
+constexpr int kMaxP = ((kMaxNg / 2 + 1) + 3) / 4 * 4;
+constexpr size_t kSpecBytes = sizeof(float2) * kMaxNg * kMaxNg * kMaxP;
+constexpr size_t kAccOff = kSpecBytes;                              // double[2 * kMaxNg]
+constexpr size_t kCntOff = kAccOff + sizeof(double) * 2 * kMaxNg;   // uint64[kMaxNg]
+constexpr size_t kTwOff = kCntOff + sizeof(unsigned long long) * kMaxNg;  // float2[kMaxNg]
+constexpr size_t kScratchBytes = kTwOff + sizeof(float2) * kMaxNg;
+static_assert(kAccOff % 256 == 0, "scratch regions must stay aligned");
+
+static __device__ __align__(256) unsigned char g_power_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+std::vector<float2> g_tw[kMaxNg + 1];  // host twiddle tables by mesh size (kept for async copies)
+
+// Device address of the scratch array on the current device (looked up on the first call).
+int scratch_address(unsigned char** out) {
+  int dev = 0;
+  COLA_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(COLA_EINVAL, "cola_power_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_power_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(COLA_ECUDA, std::string("cola_power_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  return COLA_OK;
+}
+
+}  // namespace
+}  // namespace cola
+
+using namespace cola;
+
+extern "C" int cola_power_noalloc(const float* delta, int32_t ng, double box, int32_t nbins, double* k, double* pk,
+                                  int64_t* nmodes, cola_stream stream) {
+  if (!delta || !k || !pk || !nmodes) return fail(COLA_EINVAL, "cola_power_noalloc: null array");
+  if (ng > kMaxNg)
+    return fail(COLA_EINVAL, "cola_power_noalloc: ng = " + std::to_string(ng) + " exceeds the static scratch limit of " +
+                                 std::to_string(kMaxNg) + " cells per side; use cola_power with a workspace");
+  if (ng < 32 || !fft_size_supported(ng)) return fail(COLA_EUNSUPPORTED, "cola_power_noalloc: unsupported ng");
+  if (!(box > 0)) return fail(COLA_EINVAL, "cola_power_noalloc: box must be positive");
+  if (nbins < 1 || nbins > ng) return fail(COLA_EINVAL, "cola_power_noalloc: nbins must be in [1, ng]");
+  unsigned char* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  float2* spec = reinterpret_cast<float2*>(base);
+  double* acc = reinterpret_cast<double*>(base + kAccOff);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + kCntOff);
+  float2* tw = reinterpret_cast<float2*>(base + kTwOff);
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_tw[ng].empty()) twiddle_table(ng, g_tw[ng]);
+  }
+  COLA_CUDA_CHECK(cudaMemcpyAsync(tw, g_tw[ng].data(), sizeof(float2) * ng, cudaMemcpyHostToDevice, st));
+  const int P = ((ng / 2 + 1) + 3) / 4 * 4;
+  if ((rc = fft3d_r2c(ng, P, delta, spec, tw, st))) return rc;
+  // launch_power_bin clears the accumulators left by the previous call before it adds
+  if ((rc = launch_power_bin(ng, P, box, nbins, spec, acc, cnt, st))) return rc;
+  return launch_power_finish(nbins, acc, cnt, k, pk, nmodes, st);
+}
