@@ -128,16 +128,26 @@ class ClockSampler:
 
 # ---- roofline bookkeeping ------------------------------------------------------------------------
 def algorithmic_bytes(name, n_p, ng):
-    """Minimum bytes a launch of kernel `name` must move (float32 / complex64 / int32 data)."""
+    """Minimum bytes a launch of kernel `name` must move (float32 / complex64 / int32 data).
+    H = n^2 (n/2 + 1) complex modes of a half spectrum, 8 bytes each."""
     np3, ng3 = n_p**3, ng**3
-    if name.startswith("fft_"):
-        n = int(name.rsplit("_", 1)[1])
-        half = n * n * (n // 2 + 1) * 8
-        if name.startswith("fft_cols"):
-            return 2 * half          # in-place complex column pass: read + write
-        return half + n**3 * 4       # x pass: real rows <-> half-spectrum rows
+    n = int(name.rsplit("_", 1)[1]) if name.rsplit("_", 1)[-1].isdigit() else ng
+    H = n * n * (n // 2 + 1) * 8
+    if name.startswith("fft_cols"):
+        return 2 * H                       # in-place complex column pass: read + write
+    if name.startswith("fft_x_r2c") or name.startswith("fft_x_c2r_"):
+        return H + n**3 * 4                # real rows <-> half-spectrum rows
+    if name.startswith("deposit_fftx"):
+        return 16 * np3 + H                # index + displacement per particle, half spectrum out
+    if name.startswith("fft_z_green"):
+        return H + 2 * H                   # delta_k in; B and Gz out
+    if name.startswith("fft_y_inv3"):
+        return 2 * H + 3 * H               # B, Gz in; C, Gy, Gz out
+    if name.startswith("fft_x_c2r3"):
+        return 3 * (H + n**3 * 4)          # three half spectra in, three real meshes out
     table = {
         "deposit_4x4": 16 * np3 + 4 * ng3,   # idx + s per particle, delta rows written once
+        "deposit_4x2": 16 * np3 + 4 * ng3,
         "deposit_2x2": 16 * np3 + 4 * ng3,
         "kspace_force": 4 * 8 * ng * ng * (ng // 2 + 1),
         "gather_kick_drift": 72 * np3 + 12 * ng3,  # s, v, s1, s2 in, s, v out; 3 force meshes once

@@ -41,8 +41,8 @@ static size_t layout(cola_plan* p, char* base) {
   w.counts = (int*)take(sizeof(int) * p->tiles.nbins);
   w.offsets = (int*)take(sizeof(int) * (p->tiles.nbins + 1));
   w.cursor = (int*)take(sizeof(int) * p->tiles.nbins);
-  w.pk_acc = (double*)take(sizeof(double) * 2 * ng);
-  w.pk_cnt = (unsigned long long*)take(sizeof(unsigned long long) * ng);
+  w.scan_blocks = (int*)take(sizeof(int) * scan_block_count(p->tiles));
+  w.pk_partial = (double*)take(sizeof(double) * power_partial_doubles((int)ng));
   // mesh region: the PM step and the initial conditions reuse the same bytes
   const size_t region = off;
   const size_t half_g = sizeof(float2) * ng * ng * p->Pg;
@@ -71,7 +71,7 @@ static int bin_particles(cola_plan* p, const float* s, cudaStream_t st) {
   Workspace& w = p->ws;
   int rc = launch_keys(p->geo, p->tiles, s, w.keys, w.counts, w.err, st);
   if (rc) return rc;
-  rc = launch_scan(p->tiles, w.counts, w.offsets, w.cursor, st);
+  rc = launch_scan(p->tiles, w.counts, w.offsets, w.cursor, w.scan_blocks, st);
   if (rc) return rc;
   return launch_scatter(p->geo, w.keys, w.cursor, w.idx, st);
 }
@@ -79,22 +79,10 @@ static int bin_particles(cola_plan* p, const float* s, cudaStream_t st) {
 // unit force meshes g_j (freal[j]) for positions s
 static int force_meshes(cola_plan* p, const float* s, cudaStream_t st) {
   Workspace& w = p->ws;
-  const int ng = p->geo.ng;
-  const int64_t ng3 = p->ng3;
   int rc = bin_particles(p, s, st);
   if (rc) return rc;
-  float* delta = w.freal;
-  rc = launch_deposit(p->geo, p->tiles, s, w.idx, w.offsets, nullptr, delta, w.err, st);
-  if (rc) return rc;
-  rc = fft3d_r2c(ng, p->Pg, delta, w.meshA, w.tw_g, st);
-  if (rc) return rc;
-  rc = launch_kspace_force(ng, p->Pg, p->cfg.box, p->cfg.deconv, w.meshA, w.meshG[0], w.meshG[1], w.meshG[2], st);
-  if (rc) return rc;
-  for (int j = 0; j < 3; ++j) {
-    rc = fft3d_c2r(ng, p->Pg, w.meshG[j], w.freal + j * ng3, w.tw_g, 1.0f, st);
-    if (rc) return rc;
-  }
-  return COLA_OK;
+  return launch_force_passes(p->geo, p->tiles, s, w.idx, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
+                             p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
 }
 
 }  // namespace cola
@@ -143,9 +131,11 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   p->geo.ratio = (c.ng % c.np == 0) ? (int)(c.ng / c.np) : 0;
   p->geo.scale32 = (float)((double)c.ng / c.box);
   p->ng3 = c.ng * c.ng * c.ng;
-  const int t = (4 * 4 * c.ng * 8 <= 200 * 1024) ? 4 : 2;
-  p->tiles.ty = p->tiles.tz = t;
-  p->tiles.nty = p->tiles.ntz = (int)c.ng / t;
+  // deposit tiles of 4 x 2 mesh rows (y, z), each spanning the whole x extent
+  p->tiles.ty = 4;
+  p->tiles.tz = 2;
+  p->tiles.nty = (int)c.ng / 4;
+  p->tiles.ntz = (int)c.ng / 2;
   p->tiles.nbins = p->tiles.nty * p->tiles.ntz * 4;
   p->Pg = padded_half((int)c.ng);
   p->Pp = padded_half((int)c.np);
@@ -307,9 +297,8 @@ int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, do
   cudaStream_t st = (cudaStream_t)stream;
   Workspace& w = plan->ws;
   if ((rc = fft3d_r2c(plan->geo.ng, plan->Pg, delta, w.meshA, w.tw_g, st))) return rc;
-  if ((rc = launch_power_bin(plan->geo.ng, plan->Pg, plan->cfg.box, nbins, w.meshA, w.pk_acc, w.pk_cnt, st)))
-    return rc;
-  return launch_power_finish(nbins, w.pk_acc, w.pk_cnt, k, pk, nmodes, st);
+  if ((rc = launch_power_bin(plan->geo.ng, plan->Pg, plan->cfg.box, nbins, w.meshA, w.pk_partial, st))) return rc;
+  return launch_power_finish(nbins, w.pk_partial, k, pk, nmodes, st);
 }
 
 int cola_fft_r2c(cola_plan* plan, int32_t which, const float* in, float* out, cola_stream stream) {

@@ -59,9 +59,9 @@ struct Workspace {
   int* counts = nullptr;    // nbins
   int* offsets = nullptr;   // nbins + 1
   int* cursor = nullptr;    // nbins
-  // power spectrum accumulators: nbins_max x (k sum, p sum) doubles + counts
-  double* pk_acc = nullptr;
-  unsigned long long* pk_cnt = nullptr;
+  int* scan_blocks = nullptr;  // one partial sum per scan tile
+  // power spectrum per-block partial sums: kPowerBlocks x ng x 3 doubles
+  double* pk_partial = nullptr;
   // initial conditions (alias the PM meshes)
   float2* icC0 = nullptr;
   float2* icC1 = nullptr;
@@ -113,12 +113,18 @@ int fft3d_c2r(int n, int P, float2* in_destroyed, float* out, const float2* tw, 
 
 // PM kernels (pm_kernels.cu)
 int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st);
-int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, cudaStream_t st);
+int scan_block_count(const Tiles& t);
+int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* block_sums, cudaStream_t st);
 int launch_scatter(const Geometry& g, const int* keys, int* cursor, unsigned* idx, cudaStream_t st);
 int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
                    int64_t* rho, float* delta, int* err, cudaStream_t st);
 int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
                         cudaStream_t st);
+// the fused mesh passes of one force evaluation (pm_fft_kernels.cu): deposit + x r2c, y pass,
+// z pass with the Green's function, inverse y passes, inverse x passes -> F [3][ng^3]
+int launch_force_passes(const Geometry& g, const Tiles& tl, const float* s, const unsigned* idx, const int* offsets,
+                        float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv, const float2* tw,
+                        int* err, cudaStream_t st);
 // mode 0: kick + drift, 1: kick + L+ (last force evaluation), 2: write the gathered unit force to gout
 int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, float* v, const float* s1,
                              const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st);
@@ -137,10 +143,12 @@ int launch_ic_assemble(int64_t n3, float d1, float d2, const float* s1, const fl
                        cudaStream_t st);
 
 // power spectrum and utilities (power_kernels.cu)
-int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* acc,
-                     unsigned long long* cnt, cudaStream_t st);
-int launch_power_finish(int nbins, const double* acc, const unsigned long long* cnt, double* k, double* pk,
-                        int64_t* nmodes, cudaStream_t st);
+// blocks of the binning kernel (fixed, so that the per-block partial sums and their reduction
+// order, hence the result, do not depend on the launch)
+constexpr int kPowerBlocks = 304;
+int power_partial_doubles(int nbins);  // size of the partial-sum buffer
+int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st);
+int launch_power_finish(int nbins, const double* partial, double* k, double* pk, int64_t* nmodes, cudaStream_t st);
 int launch_unpad(int n, int P, const float2* in, float2* out, cudaStream_t st);
 
 }  // namespace cola

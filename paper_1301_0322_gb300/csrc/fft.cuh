@@ -166,6 +166,14 @@ struct FirstRadix<Radices<R0, Rs...>> {
   static constexpr int value = R0;
 };
 
+// padded index of the row-layout exchange buffers (one pad slot per 8 entries: the stride-R
+// stores of the first Stockham stages then fall on distinct banks); row pitch = 8 mod 16
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 3); }
+template <int M>
+__host__ __device__ constexpr int xrow_ld() {
+  return ((M + 1 + ((M + 1) >> 3) + 1) + 15) / 16 * 16 + 8;
+}
+
 // ---- Stockham stages --------------------------------------------------------------------
 template <int N, int E, int TWS, bool INV>
 struct Stockham {

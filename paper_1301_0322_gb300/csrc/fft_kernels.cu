@@ -8,11 +8,12 @@
 
 namespace cola {
 
-// columns per block of the strided passes (16 columns = 128 contiguous bytes per row), capped
-// at 512 threads per block so that every thread keeps its E elements in registers
+// columns per block of the strided passes (16 columns = 128 contiguous bytes per row); blocks
+// of at most 256 threads (512 for the longest transforms) so that two blocks fit on an SM with
+// every thread's E elements in registers, and one block's loads overlap the other's FFT
 template <int N>
 __host__ __device__ constexpr int col_width() {
-  return FFTConf<N>::T * 16 <= 512 ? 16 : (FFTConf<N>::T * 8 <= 512 ? 8 : 4);
+  return FFTConf<N>::T * 16 <= 256 ? 16 : (FFTConf<N>::T * 8 <= 256 ? 8 : (FFTConf<N>::T * 4 <= 512 ? 4 : 2));
 }
 // rows per block of the contiguous x passes (about 256 threads per block)
 template <int N>
@@ -22,7 +23,7 @@ __host__ __device__ constexpr int x_rows() {
 
 // In-place FFT of ncols columns per slab: element (n, col) at data[slab*slab_stride + n*row_stride + col].
 template <int N, bool INV>
-__global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>())
+__global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
     k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols,
                const float2* __restrict__ tw) {
   constexpr int W = col_width<N>();
@@ -45,21 +46,21 @@ __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>())
 template <int N>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
     k_fft_x_r2c(const float* __restrict__ in, float2* __restrict__ out, int P, const float2* __restrict__ tw) {
-  constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = M + 1;
+  constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
   extern __shared__ float2 smem[];
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = reinterpret_cast<const float2*>(in + row * N);
   float2* buf = smem + w * LD;
   auto load = [&](int n) -> float2 { return src[n]; };
-  auto mem = [&](int n) -> float2& { return buf[n]; };
-  auto store = [&](int n, float2 x) { buf[n] = x; };
+  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
+  auto store = [&](int n, float2 x) { buf[xpad(n)] = x; };
   fft_1d<M, 2, false>(t, tw, load, mem, store);
   __syncthreads();
   float2* dst = out + row * P;
   for (int k = t; k <= M; k += T) {
-    const float2 a = buf[k == M ? 0 : k];
-    const float2 b = c_conj(buf[k == 0 ? 0 : M - k]);
+    const float2 a = buf[xpad(k == M ? 0 : k)];
+    const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
     const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
     const float2 d = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
     const float2 o = make_float2(d.y, -d.x);  // -i d
@@ -72,21 +73,21 @@ template <int N>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
     k_fft_x_c2r(const float2* __restrict__ in, float* __restrict__ out, int P, const float2* __restrict__ tw,
                 float scale) {
-  constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = M + 1;
+  constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
   extern __shared__ float2 smem[];
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = in + row * P;
   float2* buf = smem + w * LD;
-  for (int k = t; k <= M; k += T) buf[k] = src[k];
+  for (int k = t; k <= M; k += T) buf[xpad(k)] = src[k];
   __syncthreads();
   auto load = [&](int n) -> float2 {
-    const float2 a = buf[n], b = c_conj(buf[M - n]);
+    const float2 a = buf[xpad(n)], b = c_conj(buf[xpad(M - n)]);
     const float2 e = c_add(a, b);
     const float2 o = c_mul(c_sub(a, b), c_conj(__ldg(tw + n)));
     return make_float2(e.x - o.y, e.y + o.x);  // e + i o
   };
-  auto mem = [&](int n) -> float2& { return buf[n]; };
+  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
   float2* dst = reinterpret_cast<float2*>(out + row * N);
   auto store = [&](int n, float2 x) { dst[n] = c_scale(x, scale); };
   fft_1d<M, 2, true>(t, tw, load, mem, store);
@@ -105,13 +106,13 @@ static const char* label(const char* kind) {
 
 template <class K>
 static void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 32 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int N>
 static int x_r2c(const float* in, float2* out, int64_t nrows, int P, const float2* tw, cudaStream_t st) {
   constexpr int M = N / 2, RB = x_rows<N>();
-  const size_t smem = (size_t)RB * (M + 1) * sizeof(float2);
+  const size_t smem = (size_t)RB * xrow_ld<M>() * sizeof(float2);
   if (nrows % RB) return fail(COLA_EINVAL, "fft x pass: row count not a multiple of the block rows");
   allow_smem(k_fft_x_r2c<N>, smem);
   { LaunchScope ls_(label<N>("r2c"), st);
@@ -123,7 +124,7 @@ static int x_r2c(const float* in, float2* out, int64_t nrows, int P, const float
 template <int N>
 static int x_c2r(const float2* in, float* out, int64_t nrows, int P, const float2* tw, float scale, cudaStream_t st) {
   constexpr int M = N / 2, RB = x_rows<N>();
-  const size_t smem = (size_t)RB * (M + 1) * sizeof(float2);
+  const size_t smem = (size_t)RB * xrow_ld<M>() * sizeof(float2);
   if (nrows % RB) return fail(COLA_EINVAL, "fft x pass: row count not a multiple of the block rows");
   allow_smem(k_fft_x_c2r<N>, smem);
   { LaunchScope ls_(label<N>("c2r"), st);

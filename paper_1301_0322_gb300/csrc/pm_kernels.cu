@@ -43,40 +43,68 @@ __global__ void k_keys(Geometry g, Tiles tl, const float* __restrict__ s, int* _
   if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
-// Exclusive scan of the bin counts (single block); resets the counts for the next use.
-__global__ void __launch_bounds__(1024) k_scan(int n, int* __restrict__ counts, int* __restrict__ offsets,
-                                               int* __restrict__ cursor) {
-  __shared__ int warp_sums[32];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int chunk = (n + blockDim.x - 1) / blockDim.x;
-  const int b0 = min(n, tid * chunk), b1 = min(n, b0 + chunk);
-  int local = 0;
-  for (int b = b0; b < b1; ++b) local += counts[b];
-  int incl = local;
+// Exclusive scan of the bin counts in three launches (block sums, scan of the block sums,
+// per-block scan); resets the counts for the next use.  kScanTile bins per block.
+constexpr int kScanTile = 1024;
+
+// inclusive block scan of one int per thread (blockDim.x == 1024)
+__device__ __forceinline__ int block_inclusive_scan(int x, int* warp_sums) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  if (lane == 31) warp_sums[wid] = incl;
+  if (lane == 31) warp_sums[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+    int ws = warp_sums[lane];
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, ws, o);
       if (lane >= o) ws += y;
     }
-    warp_sums[lane] = ws;  // inclusive over warps
+    warp_sums[lane] = ws;
   }
   __syncthreads();
-  int run = incl - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  return x + (wid > 0 ? warp_sums[wid - 1] : 0);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_reduce(int n, const int* __restrict__ counts, int* __restrict__ block_sums) {
+  __shared__ int warp_sums[32];
+  const int i = blockIdx.x * kScanTile + threadIdx.x;
+  const int x = i < n ? counts[i] : 0;
+  const int incl = block_inclusive_scan(x, warp_sums);
+  if (threadIdx.x == kScanTile - 1) block_sums[blockIdx.x] = incl;
+}
+
+// exclusive scan of nb block sums in place (single block; nb <= 1024 * per)
+__global__ void __launch_bounds__(1024) k_scan_blocks(int nb, int* __restrict__ block_sums) {
+  __shared__ int warp_sums[32];
+  const int per = (nb + 1023) / 1024;
+  const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+  int local = 0;
+  for (int b = b0; b < b1; ++b) local += block_sums[b];
+  int run = block_inclusive_scan(local, warp_sums) - local;
   for (int b = b0; b < b1; ++b) {
-    const int c = counts[b];
-    offsets[b] = run;
-    cursor[b] = run;
-    counts[b] = 0;
+    const int c = block_sums[b];
+    block_sums[b] = run;
     run += c;
   }
-  if (tid == blockDim.x - 1) offsets[n] = warp_sums[(blockDim.x >> 5) - 1];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ counts, const int* __restrict__ block_sums,
+                                                    int* __restrict__ offsets, int* __restrict__ cursor) {
+  __shared__ int warp_sums[32];
+  const int i = blockIdx.x * kScanTile + threadIdx.x;
+  const int x = i < n ? counts[i] : 0;
+  const int excl = block_inclusive_scan(x, warp_sums) - x + block_sums[blockIdx.x];
+  if (i < n) {
+    offsets[i] = excl;
+    cursor[i] = excl;
+    counts[i] = 0;
+  }
+  if (i == n - 1) offsets[n] = excl + x;
 }
 
 __global__ void k_scatter(int64_t np3, const int* __restrict__ keys, int* __restrict__ cursor,
@@ -290,9 +318,24 @@ int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, in
   return COLA_OK;
 }
 
-int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, cudaStream_t st) {
-  { LaunchScope ls_("scan", st);
-  k_scan<<<1, 1024, 0, st>>>(t.nbins, counts, offsets, cursor); }
+int scan_block_count(const Tiles& t) { return (t.nbins + kScanTile - 1) / kScanTile; }
+
+int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* block_sums, cudaStream_t st) {
+  const int nb = scan_block_count(t);
+  {
+    LaunchScope ls_("scan_reduce", st);
+    k_scan_reduce<<<nb, kScanTile, 0, st>>>(t.nbins, counts, block_sums);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("scan_blocks", st);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nb, block_sums);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("scan_apply", st);
+    k_scan_apply<<<nb, kScanTile, 0, st>>>(t.nbins, counts, block_sums, offsets, cursor);
+  }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
@@ -309,11 +352,11 @@ static int deposit_t(const Geometry& g, const Tiles& t, const float* s, const un
                      int64_t* rho, float* delta, int* err, cudaStream_t st) {
   const size_t smem = (size_t)TY * TZ * g.ng * sizeof(unsigned long long);
   if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "deposit tile does not fit in shared memory");
-  if (smem > 48 * 1024)
+  if (smem > 32 * 1024)
     COLA_CUDA_CHECK(cudaFuncSetAttribute(k_deposit<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double ng3 = (double)g.ng * g.ng * g.ng;
   const float dscale = (float)(ng3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
-  { LaunchScope ls_(TY == 4 ? "deposit_4x4" : "deposit_2x2", st);
+  { LaunchScope ls_(TY == 2 ? "deposit_2x2" : (TZ == 2 ? "deposit_4x2" : "deposit_4x4"), st);
   k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, s, idx, offsets, rho, delta, dscale, err); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
@@ -322,6 +365,7 @@ static int deposit_t(const Geometry& g, const Tiles& t, const float* s, const un
 int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
                    int64_t* rho, float* delta, int* err, cudaStream_t st) {
   if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, s, idx, offsets, rho, delta, err, st);
+  if (t.ty == 4 && t.tz == 2) return deposit_t<4, 2>(g, t, s, idx, offsets, rho, delta, err, st);
   if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, s, idx, offsets, rho, delta, err, st);
   return fail(COLA_EUNSUPPORTED, "deposit: unsupported tile shape");
 }

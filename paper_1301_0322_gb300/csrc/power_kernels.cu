@@ -20,67 +20,89 @@ __device__ __forceinline__ float sinc_pi_p(int n, int ng) {
   return sinpif(x) / (3.14159265358979323846f * x);
 }
 
-// acc[2 b] += sum w |k|, acc[2 b + 1] += sum w P(k), cnt[b] += sum w, for shells b = 1..nbins
-// (stored at b - 1).  Lanes of a warp that share a shell are summed by their leader in lane
-// order, so each warp issues one float64 atomic per distinct shell.
+// Power-spectrum binning.  A warp takes 32 consecutive k_x of one (k_y, k_z) row; lanes in
+// the same shell are contiguous, so a segmented shuffle reduction (float32, at most 31 adds)
+// leaves each shell's sum in its first lane, which adds it in float64 to the warp's own
+// shared-memory accumulators (no atomics).  Each block then writes its per-shell totals in a
+// fixed order and k_power_finish adds the blocks in block order: the result is deterministic.
+// partial layout: [block][shell][3] = (sum w |k|, sum w P, sum w).
 __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, const float2* __restrict__ dk,
-                            double* __restrict__ acc, unsigned long long* __restrict__ cnt) {
+                            double* __restrict__ partial) {
+  extern __shared__ double pacc[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nh = ng / 2 + 1;
-  const int64_t total = (int64_t)ng * ng * nh;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    int b = -1;
-    float kw = 0.f, pw = 0.f;
-    int w = 0;
-    if (i < total) {
-      const int kx = (int)(i % nh);
-      const int64_t r = i / nh;
-      const int ky = (int)(r % ng), kz = (int)(r / ng);
-      const int nx = kx, ny = ky < ng / 2 ? ky : ky - ng, nz = kz < ng / 2 ? kz : kz - ng;
-      const int m = nx * nx + ny * ny + nz * nz;
-      const int sb = shell_of(m);
-      if (sb >= 1 && sb <= nbins) {
-        b = sb - 1;
-        w = (nx == 0 || nx == ng / 2) ? 1 : 2;
-        const float2 d = dk[r * P + kx];
-        const float sx = sinc_pi_p(nx, ng), sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
-        const float win = (sx * sx) * (sy * sy) * (sz * sz);
-        const float p = (d.x * d.x + d.y * d.y) * pnorm / (win * win);
-        kw = w * kf * sqrtf((float)m);
-        pw = w * p;
+  for (int i = threadIdx.x; i < nwarps * nbins * 3; i += blockDim.x) pacc[i] = 0.0;
+  __syncthreads();
+  double* mine = pacc + (size_t)warp * nbins * 3;
+  const int64_t nrows = (int64_t)ng * ng;
+  for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < nrows; row += (int64_t)gridDim.x * nwarps) {
+    const int ky = (int)(row % ng), kz = (int)(row / ng);
+    const int ny = ky < ng / 2 ? ky : ky - ng, nz = kz < ng / 2 ? kz : kz - ng;
+    const int myz = ny * ny + nz * nz;
+    const float sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
+    const float wyz = (sy * sy) * (sz * sz);
+    const float2* rowp = dk + row * P;
+    for (int c0 = 0; c0 < nh; c0 += 32) {
+      const int kx = c0 + lane;
+      int b = -1;
+      float kw = 0.f, pw = 0.f, w = 0.f;
+      if (kx < nh) {
+        const int m = kx * kx + myz;
+        const int sb = shell_of(m);
+        if (sb >= 1 && sb <= nbins) {
+          b = sb - 1;
+          w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
+          const float2 d = rowp[kx];
+          const float sx = sinc_pi_p(kx, ng);
+          const float win = (sx * sx) * wyz;
+          kw = w * kf * sqrtf((float)m);
+          pw = w * (d.x * d.x + d.y * d.y) * pnorm / (win * win);
+        }
       }
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    const int leader = __ffs(peers) - 1;
-    double ks = 0.0, ps = 0.0;
-    unsigned long long cs = 0;
-    for (int l = 0; l < 32; ++l) {
-      const float kl = __shfl_sync(0xffffffffu, kw, l);
-      const float pl = __shfl_sync(0xffffffffu, pw, l);
-      const int wl = __shfl_sync(0xffffffffu, w, l);
-      if ((peers >> l) & 1u) {
-        ks += (double)kl;
-        ps += (double)pl;
-        cs += (unsigned long long)wl;
+      // segmented reduction toward the first lane of each run of equal shells
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int bo = __shfl_down_sync(0xffffffffu, b, o);
+        const float ko = __shfl_down_sync(0xffffffffu, kw, o);
+        const float po = __shfl_down_sync(0xffffffffu, pw, o);
+        const float wo = __shfl_down_sync(0xffffffffu, w, o);
+        if (lane + o < 32 && bo == b) {
+          kw += ko;
+          pw += po;
+          w += wo;
+        }
       }
+      const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
+      if (b >= 0 && (lane == 0 || bprev != b)) {
+        mine[3 * b] += (double)kw;
+        mine[3 * b + 1] += (double)pw;
+        mine[3 * b + 2] += (double)w;
+      }
+      __syncwarp();
     }
-    if (b >= 0 && lane == leader) {
-      atomicAdd(&acc[2 * b], ks);
-      atomicAdd(&acc[2 * b + 1], ps);
-      atomicAdd(&cnt[b], cs);
-    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nbins * 3; i += blockDim.x) {
+    double t = 0.0;
+    for (int wv = 0; wv < nwarps; ++wv) t += pacc[(size_t)wv * nbins * 3 + i];
+    partial[(size_t)blockIdx.x * nbins * 3 + i] = t;
   }
 }
 
-__global__ void k_power_finish(int nbins, const double* __restrict__ acc, const unsigned long long* __restrict__ cnt,
-                               double* __restrict__ k, double* __restrict__ pk, int64_t* __restrict__ nmodes) {
+__global__ void k_power_finish(int nbins, int nblocks, const double* __restrict__ partial, double* __restrict__ k,
+                               double* __restrict__ pk, int64_t* __restrict__ nmodes) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbins) return;
-  const unsigned long long c = cnt[b];
-  k[b] = c ? acc[2 * b] / (double)c : 0.0;
-  pk[b] = c ? acc[2 * b + 1] / (double)c : 0.0;
-  nmodes[b] = (int64_t)c;
+  double ks = 0.0, ps = 0.0, cs = 0.0;
+  for (int blk = 0; blk < nblocks; ++blk) {
+    const double* r = partial + ((size_t)blk * nbins + b) * 3;
+    ks += r[0];
+    ps += r[1];
+    cs += r[2];
+  }
+  k[b] = cs > 0 ? ks / cs : 0.0;
+  pk[b] = cs > 0 ? ps / cs : 0.0;
+  nmodes[b] = (int64_t)cs;
 }
 
 __global__ void k_unpad(int n, int P, const float2* __restrict__ in, float2* __restrict__ out) {
@@ -92,25 +114,34 @@ __global__ void k_unpad(int n, int P, const float2* __restrict__ in, float2* __r
   }
 }
 
-int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* acc, unsigned long long* cnt,
-                     cudaStream_t st) {
-  COLA_CUDA_CHECK(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * nbins, st));
-  COLA_CUDA_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nbins, st));
+static int power_warps(int nbins) {
+  const int w = (int)((160 * 1024) / ((size_t)nbins * 3 * sizeof(double)));
+  return std::max(1, std::min(8, w));
+}
+
+int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * 3; }
+
+int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st) {
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const double ng6 = std::pow((double)ng, 6.0);
   const float pnorm = (float)(box * box * box / ng6);
-  const int64_t total = (int64_t)ng * ng * (ng / 2 + 1);
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  { LaunchScope ls_("power_bin", st);
-  k_power_bin<<<blocks, 256, 0, st>>>(ng, P, kf, pnorm, nbins, dk, acc, cnt); }
+  const int warps = power_warps(nbins);
+  const size_t smem = (size_t)warps * nbins * 3 * sizeof(double);
+  if (smem > 32 * 1024)
+    COLA_CUDA_CHECK(cudaFuncSetAttribute(k_power_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    LaunchScope ls_("power_bin", st);
+    k_power_bin<<<kPowerBlocks, 32 * warps, smem, st>>>(ng, P, kf, pnorm, nbins, dk, partial);
+  }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 
-int launch_power_finish(int nbins, const double* acc, const unsigned long long* cnt, double* k, double* pk,
-                        int64_t* nmodes, cudaStream_t st) {
-  { LaunchScope ls_("power_finish", st);
-  k_power_finish<<<(nbins + 127) / 128, 128, 0, st>>>(nbins, acc, cnt, k, pk, nmodes); }
+int launch_power_finish(int nbins, const double* partial, double* k, double* pk, int64_t* nmodes, cudaStream_t st) {
+  {
+    LaunchScope ls_("power_finish", st);
+    k_power_finish<<<(nbins + 127) / 128, 128, 0, st>>>(nbins, kPowerBlocks, partial, k, pk, nmodes);
+  }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }

@@ -9,7 +9,7 @@
 //
 // The scratch (the half spectrum, the shell accumulators and the twiddle table) lives in the
 // file-scope device array below, sized for meshes up to COLA_NOALLOC_MAX_NG^3.  Every GPU that
-// loads this library keeps that array (about 8.5 MiB) until the process exits.  Host code must
+// loads this library keeps that array (about 9.4 MiB) until the process exits.  Host code must
 // not pass the array's name to a kernel: on the host that name is only a stand-in for the
 // device symbol, so its device address is looked up once per device with
 // cudaGetSymbolAddress and that address is what the kernels receive.
@@ -24,11 +24,10 @@ namespace {
 constexpr int kMaxNg = COLA_NOALLOC_MAX_NG;
 constexpr int kMaxP = ((kMaxNg / 2 + 1) + 3) / 4 * 4;
 constexpr size_t kSpecBytes = sizeof(float2) * kMaxNg * kMaxNg * kMaxP;
-constexpr size_t kAccOff = kSpecBytes;                              // double[2 * kMaxNg]
-constexpr size_t kCntOff = kAccOff + sizeof(double) * 2 * kMaxNg;   // uint64[kMaxNg]
-constexpr size_t kTwOff = kCntOff + sizeof(unsigned long long) * kMaxNg;  // float2[kMaxNg]
+constexpr size_t kPartOff = kSpecBytes;  // per-block shell sums: double[kPowerBlocks * kMaxNg * 3]
+constexpr size_t kTwOff = kPartOff + sizeof(double) * kPowerBlocks * kMaxNg * 3;  // float2[kMaxNg]
 constexpr size_t kScratchBytes = kTwOff + sizeof(float2) * kMaxNg;
-static_assert(kAccOff % 256 == 0, "scratch regions must stay aligned");
+static_assert(kPartOff % 256 == 0 && kTwOff % 256 == 0, "scratch regions must stay aligned");
 
 static __device__ __align__(256) unsigned char g_power_scratch[kScratchBytes];
 
@@ -73,8 +72,7 @@ extern "C" int cola_power_noalloc(const float* delta, int32_t ng, double box, in
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   float2* spec = reinterpret_cast<float2*>(base);
-  double* acc = reinterpret_cast<double*>(base + kAccOff);
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + kCntOff);
+  double* partial = reinterpret_cast<double*>(base + kPartOff);
   float2* tw = reinterpret_cast<float2*>(base + kTwOff);
   {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -83,7 +81,8 @@ extern "C" int cola_power_noalloc(const float* delta, int32_t ng, double box, in
   COLA_CUDA_CHECK(cudaMemcpyAsync(tw, g_tw[ng].data(), sizeof(float2) * ng, cudaMemcpyHostToDevice, st));
   const int P = ((ng / 2 + 1) + 3) / 4 * 4;
   if ((rc = fft3d_r2c(ng, P, delta, spec, tw, st))) return rc;
-  // launch_power_bin clears the accumulators left by the previous call before it adds
-  if ((rc = launch_power_bin(ng, P, box, nbins, spec, acc, cnt, st))) return rc;
-  return launch_power_finish(nbins, acc, cnt, k, pk, nmodes, st);
+  // the binning kernel overwrites every partial sum it later reads, so what the previous call
+  // left in the scratch never enters this result
+  if ((rc = launch_power_bin(ng, P, box, nbins, spec, partial, st))) return rc;
+  return launch_power_finish(nbins, partial, k, pk, nmodes, st);
 }

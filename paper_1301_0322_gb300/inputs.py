@@ -12,6 +12,7 @@ import numpy as np
 WORKLOADS = {
     "cola_32p_64g_L100": (32, 64, 100.0, 1),
     "cola_256p_768g_L100": (256, 768, 100.0, 2),
+    "cola_128p_384g_L50": (128, 384, 50.0, 2),  # 1/8 sub-volume of the above (profiling captures)
     "cola_128p_256g_L200": (128, 256, 200.0, 7),
     "cola_1024p_2048g_L1000": (1024, 2048, 1000.0, 3),
 }
