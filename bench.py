@@ -40,6 +40,7 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -380,6 +381,13 @@ def gb300_arm(args):
         e2e = {"value": world * n3 * NSTEPS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": 4 * n3, "d2h_bytes_per_step": 2 * 12 * n3 + 8 * nbins}
 
+    # forward + adjoint on the differentiable workload, through the autograd wrapper
+    fwd_adj = None
+    if not args.no_adjoint:
+        del plan
+        torch.cuda.empty_cache()
+        fwd_adj = adjoint_timing(args, dev, rank, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         reps, vals, desc, spent = 0, [], "", 0.0
@@ -400,7 +408,7 @@ def gb300_arm(args):
                        "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations + density + P(k)",
                        "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (meshes of several GB)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fwd_adjoint": fwd_adj,
             "gpu_launches": int(cnt1.value - cnt0.value),
             "kernels": {kk: {"launches": kv["launches"], "ms_per_step": kv["ms"] / args.steps,
                              "share": round(kv["share"], 4)} for kk, kv in
@@ -408,6 +416,55 @@ def gb300_arm(args):
         }
         print(json.dumps(line), flush=True)
     barrier(world)
+
+
+def adjoint_timing(args, dev, rank, world):
+    """Particle-updates/s of forward + gradient (loss = sum (delta - delta_target)^2, gradient
+    with respect to the white noise) on the 128^3 / 256^3, L = 200 Mpc/h workload, and the cost
+    of the backward pass relative to the forward pass."""
+    import torch
+
+    import paper_1301_0322_gb300 as cola
+    from paper_1301_0322_gb300 import inputs
+
+    name = "cola_128p_256g_L200"
+    n_p, ng, box, seed = inputs.WORKLOADS[name]
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=NSTEPS, adjoint=True, device=dev, **inputs.COSMOLOGY)
+    with torch.no_grad():
+        target = cola.cola_density_from_noise(plan.noise(seed), plan).double()
+    noise = plan.noise(seed + 1000 + rank)
+    stream = torch.cuda.current_stream()
+
+    def fwd_bwd():
+        x = noise.clone().requires_grad_(True)
+        loss = ((cola.cola_density_from_noise(x, plan).double() - target) ** 2).sum()
+        loss.backward()
+        return x.grad
+
+    def fwd_only():
+        with torch.no_grad():
+            return ((cola.cola_density_from_noise(noise, plan).double() - target) ** 2).sum()
+
+    for _ in range(max(3, args.warmup)):
+        fwd_bwd()
+        fwd_only()
+    torch.cuda.synchronize()
+    barrier(world)
+    k = max(3, min(args.steps, 20))
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(k):
+        fwd_bwd()
+    e1.record(stream)
+    for _ in range(k):
+        fwd_only()
+    e2.record(stream)
+    e2.synchronize()
+    ms_fb = max_over_ranks(e0.elapsed_time(e1) / k, world, dev)
+    ms_f = max_over_ranks(e1.elapsed_time(e2) / k, world, dev)
+    return {"value": world * n_p**3 * NSTEPS / (ms_fb * 1e-3), "unit": UNIT, "workload": name,
+            "ms_per_step": ms_fb, "forward_ms": ms_f, "backward_over_forward": (ms_fb - ms_f) / ms_f,
+            "step": "forward with per-evaluation checkpoints + density + loss + adjoint to the noise"}
 
 
 if __name__ == "__main__":

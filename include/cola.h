@@ -70,6 +70,7 @@ typedef struct {
   double a_final;     /* final scale factor (1.0)                                            */
   int32_t deconv;     /* CIC deconvolution power p in 1/W(k)^p of the force: 0, 1 (default), 2 */
   int32_t fixed_bits; /* F: CIC positions are quantised to 2^-F cell (default 16, 8..20)      */
+  int32_t adjoint;    /* 1: also reserve the workspace of cola_step_adjoint (3 more meshes)      */
 } cola_config;
 
 /* Fill *cfg with the 32^3-particle / 64^3-mesh defaults (L = 100 Mpc/h, Om = 0.27, OL = 0.73,
@@ -128,6 +129,29 @@ int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1
  * CIC deposit -> FFT -> i k_j / (k^2 W^p) -> inverse FFT -> CIC gather.
  * s: device float32 [3][np^3]; g: device float32 [3][np^3] output. */
 int cola_force(cola_plan* plan, const float* s, float* g, cola_stream stream);
+
+/* Reverse-mode derivatives (the paper has none; these are the exact transposes of the
+ * forward calls, with the CIC weights differentiated almost everywhere at the forward path's
+ * quantised positions).  They propagate adjoints lam_* = dLoss/d(*) backwards:
+ *
+ * cola_step_adjoint: transpose of cola_step(step).  s_ckpt: the displacements cola_step(step)
+ * started from (device float32 [3][np^3], read only).  On entry lam_s, lam_v hold the adjoints
+ * of the step's outputs (s, v); on exit, of its inputs.  lam_s1, lam_s2 accumulate (+=) the
+ * adjoints of s1, s2.  Needs a plan created with cola_config.adjoint = 1 (COLA_EINVAL
+ * otherwise).  Run it for step = nsteps .. 0 with the matching checkpoints.
+ *
+ * cola_density_adjoint: lam_s = (d delta / d s)^T delta_bar for the float density of
+ * cola_density (delta_bar: device float32 [ng^3]; lam_s: device float32 [3][np^3], written).
+ *
+ * cola_ic_2lpt_adjoint: transpose of cola_ic_2lpt.  lam_s: adjoint of the initial s (read);
+ * lam_s1, lam_s2: the accumulated adjoints of s1, s2 (read and overwritten: they get
+ * lam_s's D1(a_init), D2(a_init) share added); grad_noise: device float32 [np^3], the
+ * derivative with respect to the white noise (written). */
+int cola_step_adjoint(cola_plan* plan, int32_t step, const float* s_ckpt, float* lam_s, float* lam_v, float* lam_s1,
+                      float* lam_s2, cola_stream stream);
+int cola_density_adjoint(cola_plan* plan, const float* s, const float* delta_bar, float* lam_s, cola_stream stream);
+int cola_ic_2lpt_adjoint(cola_plan* plan, const float* noise, const float* lam_s, float* lam_s1, float* lam_s2,
+                         float* grad_noise, cola_stream stream);
 
 /* CIC density of the particles at displacements s (Sec. 3.1 analysis; the deposit of the
  * force).  rho_fix (may be NULL): device int64 [ng^3], sum of integer CIC weights with

@@ -47,7 +47,7 @@ def acceleration(s, cfg, a):
     return 1.5 * cfg.cosmo.omega_m * a * g
 
 
-def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=None):
+def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=None, record=None):
     """Evolve from the 2LPT initial conditions at a_init to a_final.
 
     Returns dict with s (displacement), v (velocity T[s] in the lab frame after L+ for the COLA
@@ -56,7 +56,8 @@ def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=Non
     ``offset`` translates every initial position by the same vector (a symmetry of the
     periodic problem; the tests use it to move lattice particles off the mesh nodes).
     ``accel_fn(s, a)`` replaces the PM acceleration (the tests use the exact 2LPT force to
-    check the Kick/Drift/L+- operators on their own)."""
+    check the Kick/Drift/L+- operators on their own).  If ``record`` is a list, the
+    displacement of every force evaluation is appended to it (checkpoints for the adjoint)."""
     if accel_fn is None:
         accel_fn = lambda s_, a_: acceleration(s_, cfg, a_)
     cosmo = cfg.cosmo
@@ -95,10 +96,14 @@ def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=Non
         return s + coef * v + (D1[i + 1] - D1[i]) * s1_frame + (D2[i + 1] - D2[i]) * s2_frame
 
     nrun = cfg.nsteps if stop_after is None else stop_after
+    if record is not None:
+        record.append(s.copy())
     accel = accel_fn(s, a[0])
     for i in range(nrun):
         v = kick(v, a[i], mid[i], i, accel)              # K(a_i, a_{i+1/2}; a_i)
         s = drift(s, v, i)                                # D(a_i, a_{i+1}; a_{i+1/2})
+        if record is not None:
+            record.append(s.copy())
         accel = accel_fn(s, a[i + 1])                     # force at the new positions
         v = kick(v, mid[i], a[i + 1], i + 1, accel)       # K(a_{i+1/2}, a_{i+1}; a_{i+1})
     if lpt:

@@ -37,7 +37,7 @@ class cola_config(ctypes.Structure):
     _fields_ = [("np", ctypes.c_int64), ("ng", ctypes.c_int64), ("box", ctypes.c_double),
                 ("cosmo", cola_cosmo), ("n_lpt", ctypes.c_double), ("nsteps", ctypes.c_int32),
                 ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("deconv", ctypes.c_int32),
-                ("fixed_bits", ctypes.c_int32)]
+                ("fixed_bits", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -57,6 +57,9 @@ _SIGNATURES = {
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
     "cola_status": [_P, _P],
     "cola_power_noalloc": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P],
+    "cola_step_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
+    "cola_density_adjoint": [_P, _P, _P, _P, _P],
+    "cola_ic_2lpt_adjoint": [_P, _P, _P, _P, _P, _P, _P],
     "cola_profile": [_P, ctypes.c_int32],
     "cola_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_launch_count": [_P],
@@ -172,6 +175,20 @@ def cola_fft_r2c(h, which, x, out, stream=None):
     _check(load_library().cola_fft_r2c(h, int(which), _ptr(x), _ptr(out), _stream(stream)))
 
 
+def cola_step_adjoint(h, step, s_ckpt, lam_s, lam_v, lam_s1, lam_s2, stream=None):
+    _check(load_library().cola_step_adjoint(h, int(step), _ptr(s_ckpt), _ptr(lam_s), _ptr(lam_v), _ptr(lam_s1),
+                                            _ptr(lam_s2), _stream(stream)))
+
+
+def cola_density_adjoint(h, s, delta_bar, lam_s, stream=None):
+    _check(load_library().cola_density_adjoint(h, _ptr(s), _ptr(delta_bar), _ptr(lam_s), _stream(stream)))
+
+
+def cola_ic_2lpt_adjoint(h, noise, lam_s, lam_s1, lam_s2, grad_noise, stream=None):
+    _check(load_library().cola_ic_2lpt_adjoint(h, _ptr(noise), _ptr(lam_s), _ptr(lam_s1), _ptr(lam_s2),
+                                               _ptr(grad_noise), _stream(stream)))
+
+
 def cola_status(h, stream=None):
     _check(load_library().cola_status(h, _stream(stream)))
 
@@ -181,12 +198,13 @@ class Plan:
     """A COLA plan plus its device workspace (allocated with torch on ``device``)."""
 
     def __init__(self, np_side=32, ng=64, box=100.0, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96,
-                 n_lpt=-2.5, nsteps=10, a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, device="cuda"):
+                 n_lpt=-2.5, nsteps=10, a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, adjoint=False,
+                 device="cuda"):
         cfg = cola_config_default()
         cfg.np, cfg.ng, cfg.box = int(np_side), int(ng), float(box)
         cfg.cosmo = cola_cosmo(omega_m, omega_l, h, sigma8, n_s)
         cfg.n_lpt, cfg.nsteps, cfg.a_init, cfg.a_final = float(n_lpt), int(nsteps), float(a_init), float(a_final)
-        cfg.deconv, cfg.fixed_bits = int(deconv), int(fixed_bits)
+        cfg.deconv, cfg.fixed_bits, cfg.adjoint = int(deconv), int(fixed_bits), int(bool(adjoint))
         self.cfg = cfg
         self.np, self.ng, self.nsteps = int(np_side), int(ng), int(nsteps)
         self.n3 = self.np**3
@@ -265,3 +283,54 @@ class Plan:
 
     def status(self):
         cola_status(self.handle)
+
+    # ---- reverse mode ----
+    def step_adjoint(self, i, s_ckpt, lam_s, lam_v, lam_s1, lam_s2):
+        cola_step_adjoint(self.handle, i, s_ckpt, lam_s, lam_v, lam_s1, lam_s2)
+
+    def density_adjoint(self, s, delta_bar):
+        _expect(delta_bar, torch.float32, self.ng**3, "delta_bar")
+        lam_s = self._empty((3, self.n3))
+        cola_density_adjoint(self.handle, s, delta_bar, lam_s)
+        return lam_s
+
+    def ic_adjoint(self, noise, lam_s, lam_s1, lam_s2):
+        grad = self._empty(self.n3)
+        cola_ic_2lpt_adjoint(self.handle, noise, lam_s, lam_s1, lam_s2, grad)
+        return grad
+
+
+class ColaDensity(torch.autograd.Function):
+    """delta_final(noise): 2LPT initial conditions, all force evaluations and the final CIC
+    density, differentiable with respect to the white noise.  The forward pass keeps the
+    displacement of every force evaluation (nsteps+1 checkpoints); the backward pass runs the
+    library's adjoint calls in reverse order.  The plan must have been built with adjoint=True."""
+
+    @staticmethod
+    def forward(ctx, noise, plan):
+        s, v, s1, s2 = plan.ic_2lpt(noise)
+        ckpts = torch.empty((plan.nsteps + 1, 3, plan.n3), dtype=torch.float32, device=noise.device)
+        for i in range(plan.nsteps + 1):
+            ckpts[i].copy_(s)
+            plan.step(i, s, v, s1, s2)
+        _, delta = plan.density(s, rho=False, delta=True)
+        ctx.plan = plan
+        ctx.save_for_backward(noise, s, ckpts)
+        return delta
+
+    @staticmethod
+    def backward(ctx, delta_bar):
+        noise, s, ckpts = ctx.saved_tensors
+        plan = ctx.plan
+        lam_s = plan.density_adjoint(s, delta_bar.contiguous().float())
+        lam_v = torch.zeros_like(lam_s)
+        lam_s1 = torch.zeros_like(lam_s)
+        lam_s2 = torch.zeros_like(lam_s)
+        for i in reversed(range(plan.nsteps + 1)):
+            plan.step_adjoint(i, ckpts[i], lam_s, lam_v, lam_s1, lam_s2)
+        return plan.ic_adjoint(noise, lam_s, lam_s1, lam_s2), None
+
+
+def cola_density_from_noise(noise, plan):
+    """Differentiable final CIC overdensity of a COLA run started from ``noise`` (see ColaDensity)."""
+    return ColaDensity.apply(noise, plan)

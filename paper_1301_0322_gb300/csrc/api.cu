@@ -54,8 +54,11 @@ static size_t layout(cola_plan* p, char* base) {
   const size_t half_p = sizeof(float2) * np * np * p->Pp;
   w.icC0 = (float2*)take(half_p);
   w.icC1 = (float2*)take(half_p);
-  for (int j = 0; j < 3; ++j) w.icR[j] = (float*)take(sizeof(float) * np3);
-  return std::max(off, pm_end);
+  w.icC2 = (float2*)take(half_p);
+  for (int j = 0; j < 5; ++j) w.icR[j] = (float*)take(sizeof(float) * np3);
+  off = std::max(off, pm_end);
+  w.lam_real = p->cfg.adjoint ? (float*)take(sizeof(float) * 3 * ng3) : nullptr;
+  return off;
 }
 
 static int check_ws(const cola_plan* p) {
@@ -104,6 +107,7 @@ int cola_config_default(cola_config* cfg) {
   cfg->a_final = 1.0;
   cfg->deconv = 1;
   cfg->fixed_bits = 16;
+  cfg->adjoint = 0;
   return COLA_OK;
 }
 
@@ -120,6 +124,7 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   if (!(c.a_init > 0) || !(c.a_final > c.a_init)) return fail(COLA_EINVAL, "need 0 < a_init < a_final");
   if (c.deconv < 0 || c.deconv > 2) return fail(COLA_EINVAL, "deconv must be 0, 1 or 2");
   if (c.fixed_bits < 8 || c.fixed_bits > 20) return fail(COLA_EINVAL, "fixed_bits must be in [8, 20]");
+  if (c.adjoint != 0 && c.adjoint != 1) return fail(COLA_EINVAL, "adjoint must be 0 or 1");
   if (!(c.cosmo.omega_m > 0) || !(c.cosmo.h > 0) || !(c.cosmo.sigma8 > 0))
     return fail(COLA_EINVAL, "omega_m, h and sigma8 must be positive");
   cola_plan* p = new cola_plan();
@@ -327,6 +332,111 @@ int cola_status(cola_plan* plan, cola_stream stream) {
   if (err & kErrNonFinite) return fail(COLA_EOVERFLOW, "non-finite particle displacement");
   if (err & kErrOverflow) return fail(COLA_EOVERFLOW, "fixed-point density overflow (too many particles per cell)");
   return COLA_OK;
+}
+
+int cola_step_adjoint(cola_plan* plan, int32_t step, const float* s_ckpt, float* lam_s, float* lam_v, float* lam_s1,
+                      float* lam_s2, cola_stream stream) {
+  int rc = check_ws(plan);
+  if (rc) return rc;
+  ProfilerGuard pg(&plan->prof);
+  if (!plan->cfg.adjoint) return fail(COLA_EINVAL, "plan was created without adjoint buffers (cola_config.adjoint)");
+  if (!s_ckpt || !lam_s || !lam_v || !lam_s1 || !lam_s2) return fail(COLA_EINVAL, "null array");
+  if (step < 0 || step > plan->cfg.nsteps) return fail(COLA_EINVAL, "step out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& w = plan->ws;
+  const int ng = plan->geo.ng;
+  const int64_t ng3 = plan->ng3;
+  const int mode = step == plan->cfg.nsteps ? 1 : 0;
+  const float* coef = w.coef + (size_t)step * kCoef32;
+  // adjoint of the Kick/Drift/L+ algebra: lam_v becomes the adjoint of the kicked velocity
+  if ((rc = launch_adjoint_pre(plan->geo.np3, mode, coef, lam_s, lam_v, lam_s1, lam_s2, st))) return rc;
+  // the force meshes at the checkpointed positions (term A of the force VJP)
+  if ((rc = force_meshes(plan, s_ckpt, st))) return rc;
+  // term B: deposit lam_v, apply the transposed force operator, gather with the weight gradient
+  if ((rc = launch_lambda_deposit(plan->geo, s_ckpt, lam_v, w.lam_real, st))) return rc;
+  float2* half[3] = {w.meshA, w.meshG[1], w.meshG[2]};
+  for (int j = 0; j < 3; ++j)
+    if ((rc = fft3d_r2c(ng, plan->Pg, w.lam_real + j * ng3, half[j], w.tw_g, st))) return rc;
+  if ((rc = launch_kspace_adjoint(ng, plan->Pg, plan->cfg.box, plan->cfg.deconv, half[0], half[1], half[2], st)))
+    return rc;
+  float* phi = w.lam_real;
+  if ((rc = fft3d_c2r(ng, plan->Pg, half[0], phi, w.tw_g, 1.0f, st))) return rc;
+  const double* row = &plan->coef64[(size_t)step * COLA_NCOEF];
+  const double to_cells = (double)ng / plan->cfg.box;
+  const double inv_rho_bar = (double)ng3 / (double)plan->geo.np3;
+  const double ckf = row[2] * row[1];
+  return launch_gather_adjoint(plan->geo, s_ckpt, w.freal, phi, lam_v, lam_s, (float)(ckf * to_cells),
+                               (float)(ckf * to_cells * inv_rho_bar), 0, st);
+}
+
+int cola_density_adjoint(cola_plan* plan, const float* s, const float* delta_bar, float* lam_s, cola_stream stream) {
+  int rc = check_ws(plan);
+  if (rc) return rc;
+  ProfilerGuard pg(&plan->prof);
+  if (!s || !delta_bar || !lam_s) return fail(COLA_EINVAL, "null array");
+  const double to_cells = (double)plan->geo.ng / plan->cfg.box;
+  const double inv_rho_bar = (double)plan->ng3 / (double)plan->geo.np3;
+  return launch_gather_adjoint(plan->geo, s, plan->ws.freal, delta_bar, nullptr, lam_s, 0.0f,
+                               (float)(to_cells * inv_rho_bar), 1, (cudaStream_t)stream);
+}
+
+int cola_ic_2lpt_adjoint(cola_plan* plan, const float* noise, const float* lam_s, float* lam_s1, float* lam_s2,
+                         float* grad_noise, cola_stream stream) {
+  int rc = check_ws(plan);
+  if (rc) return rc;
+  ProfilerGuard pg(&plan->prof);
+  if (!noise || !lam_s || !lam_s1 || !lam_s2 || !grad_noise) return fail(COLA_EINVAL, "null array");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& w = plan->ws;
+  const int n = plan->geo.np, P = plan->Pp;
+  const int64_t n3 = plan->geo.np3;
+  const float norm = (float)(1.0 / (double)n3);
+  const double box = plan->cfg.box;
+  const double* row0 = plan->coef64.data();
+  // s = D1 s1 + D2 s2 at a_init
+  if ((rc = launch_ic_adjoint_assemble(n3, (float)row0[10], (float)row0[11], lam_s, lam_s1, lam_s2, st))) return rc;
+  // lam_mu2 = IFFT( sum_j (+i k_j / k^2) FFT(D2u(1) lam_s2_j) ) / n^3   (transpose of s2 = D2u(1) psi2)
+  for (int j = 0; j < 3; ++j) {
+    if ((rc = fft3d_r2c(n, P, lam_s2 + j * n3, w.icC1, w.tw_p, st))) return rc;
+    if ((rc = launch_kmul_acc(n, P, box, 0, j, 0, (float)(plan->d2u1 / (double)n3), j > 0, w.icC1, w.icC2, st)))
+      return rc;
+  }
+  float* lam_mu2 = w.icR[3];
+  if ((rc = fft3d_c2r(n, P, w.icC2, lam_mu2, w.tw_p, 1.0f, st))) return rc;
+  // the linear density and the diagonal second derivatives psi_ii
+  if ((rc = fft3d_r2c(n, P, noise, w.icC0, w.tw_p, st))) return rc;
+  if ((rc = launch_ic_filter(n, P, box, plan->pk_amp, plan->cfg.cosmo.n_s, plan->cfg.cosmo.omega_m,
+                             plan->cfg.cosmo.h, w.icC0, st)))
+    return rc;
+  for (int i = 0; i < 3; ++i) {
+    if ((rc = launch_kmul(n, P, box, 1, i, i, norm, w.icC0, w.icC1, st))) return rc;
+    if ((rc = fft3d_c2r(n, P, w.icC1, w.icR[i], w.tw_p, 1.0f, st))) return rc;
+  }
+  // lam_delta_k = sum_ij M_ij FFT(lam_psi_ij) + sum_j (-i k_j / k^2) FFT(lam_s1_j)
+  float* tmp = w.icR[4];
+  for (int i = 0; i < 3; ++i) {  // lam_psi_ii = lam_mu2 * (psi_jj + psi_kk)
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    if ((rc = launch_ic_adjoint_product(n3, lam_mu2, w.icR[j], w.icR[k], tmp, st))) return rc;
+    if ((rc = fft3d_r2c(n, P, tmp, w.icC1, w.tw_p, st))) return rc;
+    if ((rc = launch_kmul_acc(n, P, box, 1, i, i, 1.0f, i > 0, w.icC1, w.icC2, st))) return rc;
+  }
+  const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (auto& ij : pairs) {  // lam_psi_ij = -2 lam_mu2 psi_ij
+    if ((rc = launch_kmul(n, P, box, 1, ij[0], ij[1], norm, w.icC0, w.icC1, st))) return rc;
+    if ((rc = fft3d_c2r(n, P, w.icC1, tmp, w.tw_p, 1.0f, st))) return rc;
+    if ((rc = launch_ic_adjoint_product(n3, lam_mu2, tmp, nullptr, tmp, st))) return rc;
+    if ((rc = fft3d_r2c(n, P, tmp, w.icC1, w.tw_p, st))) return rc;
+    if ((rc = launch_kmul_acc(n, P, box, 1, ij[0], ij[1], 1.0f, 1, w.icC1, w.icC2, st))) return rc;
+  }
+  for (int j = 0; j < 3; ++j) {
+    if ((rc = fft3d_r2c(n, P, lam_s1 + j * n3, w.icC1, w.tw_p, st))) return rc;
+    if ((rc = launch_kmul_acc(n, P, box, 0, j, 0, -1.0f, 1, w.icC1, w.icC2, st))) return rc;
+  }
+  // noise gradient = IFFT(amp(k) lam_delta_k) / n^3
+  if ((rc = launch_ic_filter(n, P, box, plan->pk_amp, plan->cfg.cosmo.n_s, plan->cfg.cosmo.omega_m,
+                             plan->cfg.cosmo.h, w.icC2, st)))
+    return rc;
+  return fft3d_c2r(n, P, w.icC2, grad_noise, w.tw_p, norm, st);
 }
 
 int cola_profile(cola_plan* plan, int32_t enable) {

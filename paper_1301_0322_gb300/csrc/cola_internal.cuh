@@ -65,7 +65,10 @@ struct Workspace {
   // initial conditions (alias the PM meshes)
   float2* icC0 = nullptr;
   float2* icC1 = nullptr;
-  float* icR[3] = {nullptr, nullptr, nullptr};
+  float2* icC2 = nullptr;
+  float* icR[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // adjoint only: three real meshes for the deposited adjoint (the first doubles as Phi)
+  float* lam_real = nullptr;
 };
 
 }  // namespace cola
@@ -141,6 +144,21 @@ int launch_source_2lpt(int64_t n3, const float* fxx, const float* fyy, const flo
 int launch_source_sub_sq(int64_t n3, const float* f, float* acc, cudaStream_t st);
 int launch_ic_assemble(int64_t n3, float d1, float d2, const float* s1, const float* s2, float* s, float* v,
                        cudaStream_t st);
+
+// adjoint kernels (adjoint_kernels.cu)
+int launch_adjoint_pre(int64_t n3, int mode, const float* coef, float* lam_s, float* lam_v, float* lam_s1,
+                       float* lam_s2, cudaStream_t st);
+int launch_lambda_deposit(const Geometry& g, const float* s, const float* lam, float* out, cudaStream_t st);
+int launch_kspace_adjoint(int ng, int P, double box, int deconv, float2* lx, const float2* ly, const float2* lz,
+                          cudaStream_t st);
+int launch_gather_adjoint(const Geometry& g, const float* s, const float* F, const float* phi, const float* lam_v,
+                          float* lam_s, float scale_a, float scale_b, int mode, cudaStream_t st);
+int launch_kmul_acc(int n, int P, double box, int kind, int i, int j, float scale, int accumulate, const float2* in,
+                    float2* out, cudaStream_t st);
+int launch_ic_adjoint_assemble(int64_t n3, float d1, float d2, const float* lam_s, float* lam_s1, float* lam_s2,
+                               cudaStream_t st);
+int launch_ic_adjoint_product(int64_t n3, const float* a, const float* b, const float* c, float* out,
+                              cudaStream_t st);
 
 // power spectrum and utilities (power_kernels.cu)
 // blocks of the binning kernel (fixed, so that the per-block partial sums and their reduction
