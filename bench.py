@@ -41,6 +41,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -383,10 +384,17 @@ def gb300_arm(args):
 
     # forward + adjoint on the differentiable workload, through the autograd wrapper
     fwd_adj = None
+    del plan
+    torch.cuda.empty_cache()
     if not args.no_adjoint:
-        del plan
-        torch.cuda.empty_cache()
         fwd_adj = adjoint_timing(args, dev, rank, world)
+        torch.cuda.empty_cache()
+
+    # the 48-box mock ensemble: batched persistent kernels + graphs against sequential single boxes
+    ens = None
+    if not args.no_ensemble:
+        ens = ensemble_timing(args, dev, rank, world)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -409,6 +417,7 @@ def gb300_arm(args):
                        "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (meshes of several GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fwd_adjoint": fwd_adj,
+            "ensemble": ens,
             "gpu_launches": int(cnt1.value - cnt0.value),
             "kernels": {kk: {"launches": kv["launches"], "ms_per_step": kv["ms"] / args.steps,
                              "share": round(kv["share"], 4)} for kk, kv in
@@ -465,6 +474,131 @@ def adjoint_timing(args, dev, rank, world):
     return {"value": world * n_p**3 * NSTEPS / (ms_fb * 1e-3), "unit": UNIT, "workload": name,
             "ms_per_step": ms_fb, "forward_ms": ms_f, "backward_over_forward": (ms_fb - ms_f) / ms_f,
             "step": "forward with per-evaluation checkpoints + density + loss + adjoint to the noise"}
+
+
+def ensemble_timing(args, dev, rank, world):
+    """Particle-updates/s of the 48-box mock ensemble (16 x 64^3/128^3 L=100, 16 x 96^3/192^3
+    L=150, 16 x 128^3/256^3 L=200 Mpc/h, seeds 100..147): noise + 2LPT IC + 11 force
+    evaluations + density + P(k) for all boxes, the steps replayed from CUDA graphs with the
+    launch shape the autotuner picked; against the same work done box after box with
+    single-box plans (one plan per box size)."""
+    import ctypes
+
+    import torch
+
+    import paper_1301_0322_gb300 as cola
+    from paper_1301_0322_gb300 import inputs
+
+    boxes = inputs.ENSEMBLE_48
+    seeds = [sd + 1000 * rank for sd in inputs.ENSEMBLE_48_SEEDS]
+    e = cola.Ensemble(boxes, device=dev, nsteps=NSTEPS, **inputs.COSMOLOGY)
+    nbins = 32
+    noise = e.noise(seeds)
+    s, v, s1, s2 = e.ic_2lpt(noise)
+    best, tune_ms = e.tune(s, reps=3)
+    delta = e._empty(e.cells_total)
+    kk, pk = e._empty((e.nbox, nbins), torch.float64), e._empty((e.nbox, nbins), torch.float64)
+    nm = e._empty((e.nbox, nbins), torch.int64)
+    h = e.handle
+    sd_arr = seeds
+
+    def ens_step():
+        cola.cola_ensemble_noise(h, sd_arr, noise)
+        cola.cola_ensemble_ic_2lpt(h, noise, s, v, s1, s2)
+        for i in range(NSTEPS + 1):
+            cola.cola_ensemble_step(h, i, s, v, s1, s2)
+        cola.cola_ensemble_density(h, s, delta)
+        cola.cola_ensemble_power(h, delta, nbins, kk, pk, nm)
+
+    stream = torch.cuda.current_stream()
+    reps = max(2, min(args.steps, 5))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
+
+    ms_ens = timed(ens_step)
+    e.status()
+    # per-kernel split of one ensemble run (direct launches with events)
+    lib = cola.load_library()
+    lib.cola_ensemble_profile(h, 1)
+    ens_step()
+    lib.cola_ensemble_profile(h, 0)
+    nmax = 64
+    names = ctypes.create_string_buffer(64 * nmax)
+    launches = (ctypes.c_int64 * nmax)()
+    msk = (ctypes.c_double * nmax)()
+    count = ctypes.c_int32()
+    lib.cola_ensemble_profile_read(h, nmax, names, launches, msk, ctypes.byref(count))
+    kernels = {}
+    for i in range(count.value):
+        nm_ = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        kernels[nm_] = {"launches": int(launches[i]), "ms": float(msk[i])}
+    peak, peak_kind = hbm_peak()
+    for name, kv in kernels.items():
+        base = name[len("ens_"):]
+        alg = 0
+        for n_p, ng, _ in boxes:
+            if base in ("keys", "scatter", "gather_kick_drift"):
+                a = algorithmic_bytes(base, n_p, ng)
+            elif base == "fft_y":
+                a = algorithmic_bytes(f"fft_cols_{ng}", n_p, ng)
+            else:
+                a = algorithmic_bytes(f"{base}_{ng}", n_p, ng)
+            alg = alg + a if a is not None and alg is not None else None
+        avg = kv["ms"] / kv["launches"]
+        kv["avg_launch_ms"] = avg
+        if alg:
+            kv["bytes_per_launch"] = alg
+            kv["achieved_gbs"] = alg / (avg * 1e-3) / 1e9
+            kv["frac"] = kv["achieved_gbs"] / peak
+    del e
+    torch.cuda.empty_cache()
+
+    # sequential single-box runs of the same 48 boxes
+    plans = {}
+    for n_p, ng, box in boxes:
+        if (n_p, ng, box) not in plans:
+            p = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=NSTEPS, device=dev, **inputs.COSMOLOGY)
+            n3 = n_p**3
+            bufs = [p._empty(n3)] + [p._empty((3, n3)) for _ in range(4)] + [p._empty(ng**3)]
+            bufs += [p._empty(nbins, torch.float64), p._empty(nbins, torch.float64), p._empty(nbins, torch.int64)]
+            plans[(n_p, ng, box)] = (p, bufs)
+
+    def seq_step():
+        for (n_p, ng, box), sd in zip(boxes, seeds):
+            p, (nz, ss, vv, a1, a2, dd, k_, p_, m_) = plans[(n_p, ng, box)]
+            hh = p.handle
+            cola.cola_noise(hh, sd, nz)
+            cola.cola_ic_2lpt(hh, nz, ss, vv, a1, a2)
+            for i in range(NSTEPS + 1):
+                cola.cola_step(hh, i, ss, vv, a1, a2)
+            cola.cola_density(hh, ss, None, dd)
+            cola.cola_power(hh, dd, nbins, k_, p_, m_)
+
+    ms_seq = timed(seq_step)
+    for p, _ in plans.values():
+        p.status()
+    updates = world * sum(b[0] ** 3 for b in boxes) * NSTEPS
+    return {"workload": "ensemble_48: 16x 64^3/128^3 L100 + 16x 96^3/192^3 L150 + 16x 128^3/256^3 L200, seeds 100..147",
+            "value": updates / (ms_ens * 1e-3), "unit": UNIT, "ms_per_step": ms_ens,
+            "sequential_single_box": {"value": updates / (ms_seq * 1e-3), "ms_per_step": ms_seq},
+            "speedup_vs_sequential": ms_seq / ms_ens,
+            "tuning": {"threads": best.threads, "tile_shape": best.tile_shape, "blocks_per_sm": best.blocks_per_sm},
+            "tune_candidates_ms": [round(float(x), 4) for x in tune_ms],
+            "step": "noise + 2LPT IC + 11 force evaluations (CUDA graph per step) + density + P(k), all boxes",
+            "kernels": {k_: {kk_: (round(vv_, 5) if isinstance(vv_, float) else vv_) for kk_, vv_ in kv.items()}
+                        for k_, kv in sorted(kernels.items(), key=lambda x: -x[1]["ms"])},
+            "peak_gbs": peak, "peak_source": peak_kind}
 
 
 if __name__ == "__main__":

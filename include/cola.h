@@ -193,6 +193,87 @@ int cola_status(cola_plan* plan, cola_stream stream);
 int cola_power_noalloc(const float* delta, int32_t ng, double box, int32_t nbins, double* k, double* pk,
                        int64_t* nmodes, cola_stream stream);
 
+/* ---- Ensembles of independent boxes -------------------------------------------------------
+ * An ensemble evolves nbox independent realisations -- boxes of different np, ng and L, the
+ * mock catalogues that motivate COLA's speed (Sec. 1, Sec. 4) -- with one launch per kernel
+ * class per force evaluation for all boxes together: persistent kernels walk a work list of
+ * (box, tile) items, so small boxes do not leave the GPU idle and there is no per-box launch
+ * cost.  Each step (cola_ensemble_step) is recorded once as a CUDA graph and replayed.
+ *
+ * Every box follows eq. ALCtimestep exactly as a single-box plan with the same cola_config
+ * does: the per-box results are those of cola_step on that box alone.
+ *
+ * Layout: the per-box particle arrays are concatenated.  Box b owns particles
+ * [poff[b], poff[b+1]) of the ensemble (poff from cola_ensemble_offsets, poff[b+1] - poff[b]
+ * = np_b^3); a [3][np^3] SoA array of box b starts at element 3 poff[b] of the ensemble array
+ * (s, v, s1, s2), a scalar per-particle array (noise) at element poff[b], and a density mesh
+ * at element moff[b] (moff[b+1] - moff[b] = ng_b^3).
+ *
+ * Requirements: 1 <= nbox <= 4096; every box has the same nsteps; ng in {64, 96, 128, 192,
+ * 256}; the total particle count below 2^31.  Other fields are free per box. */
+typedef struct cola_ensemble cola_ensemble;
+
+/* Tunable launch shape of the ensemble kernels (chosen by cola_ensemble_tune):
+ *  threads       block size of every persistent kernel, 128 or 256; it fixes the FFT
+ *                columns per block (threads / (n / E)) and the deposit tile rows
+ *  tile_shape    deposit tile (y x z rows) for a given row count: 0 = 4x4, 8x4, 8x8 for
+ *                16, 32, 64 rows; 1 = 8x2, 4x8, 16x4.  Tiles are also the particle bins.
+ *  blocks_per_sm persistent grid = blocks_per_sm x SM count, capped by occupancy; 0 = the
+ *                occupancy limit. */
+typedef struct {
+  int32_t threads;
+  int32_t tile_shape;
+  int32_t blocks_per_sm;
+} cola_ensemble_tuning;
+
+#define COLA_ENSEMBLE_TUNE_CANDIDATES 8
+
+/* Create / destroy.  boxes: host array of nbox configurations (see the requirements above). */
+int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out);
+int cola_ensemble_destroy(cola_ensemble* ens);
+/* Bytes of device workspace (all boxes' meshes and tables, the shared sort buffers). */
+int cola_ensemble_workspace_bytes(const cola_ensemble* ens, size_t* bytes);
+/* Attach a caller-owned device workspace (256-byte aligned, >= the size above) and upload the
+ * tables on `stream`.  Also creates the library's private capture stream. */
+int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes, cola_stream stream);
+/* Host arrays of nbox + 1 entries: poff (particle offsets) and moff (mesh-cell offsets). */
+int cola_ensemble_offsets(const cola_ensemble* ens, int64_t* poff, int64_t* moff);
+/* Philox white noise of every box (cola_noise with seeds[b] into noise + poff[b]). */
+int cola_ensemble_noise(cola_ensemble* ens, const uint64_t* seeds, float* noise, cola_stream stream);
+/* 2LPT initial conditions of every box (cola_ic_2lpt on each box's slices). */
+int cola_ensemble_ic_2lpt(cola_ensemble* ens, const float* noise, float* s, float* v, float* s1, float* s2,
+                          cola_stream stream);
+/* One step of eq. ALCtimestep (cola_step semantics, step = 0..nsteps) for every box: 11
+ * kernel launches in total (binning 5, fused mesh passes 5, gather + kick + drift 1), replayed
+ * from a CUDA graph recorded on the first call with these pointers and this tuning. */
+int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, const float* s1, const float* s2,
+                       cola_stream stream);
+/* CIC overdensity of every box: delta + moff[b] receives box b's mesh (cola_density). */
+int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola_stream stream);
+/* P(k) of every box (cola_power); box b writes rows [b nbins, (b+1) nbins) of k, pk, nmodes.
+ * nbins <= the smallest ng of the ensemble. */
+int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
+                        int64_t* nmodes, cola_stream stream);
+/* Autotuner: times the binning and mesh passes of one force evaluation at displacements s
+ * (read only) for each of the COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
+ * repetitions after one warm-up, CUDA events on `stream`; synchronises), keeps the fastest
+ * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
+ * milliseconds of each candidate, in the order threads in {128, 256} x tile_shape in {0, 1}
+ * x blocks_per_sm in {0, 2}.  Every candidate gives bit-identical results. */
+int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
+                       cola_stream stream);
+int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning);
+int cola_ensemble_set_tuning(cola_ensemble* ens, const cola_ensemble_tuning* tuning, cola_stream stream);
+/* Graph replay on (1, default) or off (0: every launch issued directly; used while profiling). */
+int cola_ensemble_use_graphs(cola_ensemble* ens, int32_t enable);
+/* cola_status over all boxes: the first box with a latched error decides the code. */
+int cola_ensemble_status(cola_ensemble* ens, cola_stream stream);
+/* Measurement hooks as cola_profile / cola_profile_read, for the ensemble's own kernels (the
+ * step runs without graphs while profiling is on). */
+int cola_ensemble_profile(cola_ensemble* ens, int32_t enable);
+int cola_ensemble_profile_read(cola_ensemble* ens, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                               int32_t* count);
+
 /* Measurement hooks (not part of the method).  cola_profile(plan, 1) makes every kernel the
  * plan's calls launch record a CUDA event pair on the launching stream; cola_profile_read
  * synchronises those events and returns, per kernel name (NUL-terminated, 64 bytes each in

@@ -40,6 +40,10 @@ class cola_config(ctypes.Structure):
                 ("fixed_bits", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
 
 
+class cola_ensemble_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "cola_config_default": [ctypes.POINTER(cola_config)],
@@ -64,7 +68,25 @@ _SIGNATURES = {
     "cola_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_launch_count": [_P],
     "cola_last_error": [],
+    "cola_ensemble_create": [_P, ctypes.c_int32, ctypes.POINTER(_P)],
+    "cola_ensemble_destroy": [_P],
+    "cola_ensemble_workspace_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "cola_ensemble_set_workspace": [_P, _P, ctypes.c_size_t, _P],
+    "cola_ensemble_offsets": [_P, _P, _P],
+    "cola_ensemble_noise": [_P, _P, _P, _P],
+    "cola_ensemble_ic_2lpt": [_P, _P, _P, _P, _P, _P, _P],
+    "cola_ensemble_step": [_P, ctypes.c_int32, _P, _P, _P, _P, _P],
+    "cola_ensemble_density": [_P, _P, _P, _P],
+    "cola_ensemble_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
+    "cola_ensemble_tune": [_P, _P, ctypes.c_int32, _P, _P, _P],
+    "cola_ensemble_get_tuning": [_P, _P],
+    "cola_ensemble_set_tuning": [_P, _P, _P],
+    "cola_ensemble_use_graphs": [_P, ctypes.c_int32],
+    "cola_ensemble_status": [_P, _P],
+    "cola_ensemble_profile": [_P, ctypes.c_int32],
+    "cola_ensemble_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
 }
+COLA_ENSEMBLE_TUNE_CANDIDATES = 8
 _lib = None
 
 
@@ -193,6 +215,84 @@ def cola_status(h, stream=None):
     _check(load_library().cola_status(h, _stream(stream)))
 
 
+def cola_ensemble_create(cfgs):
+    arr = (cola_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    _check(load_library().cola_ensemble_create(arr, len(cfgs), ctypes.byref(h)))
+    return h
+
+
+def cola_ensemble_destroy(h):
+    _check(load_library().cola_ensemble_destroy(h))
+
+
+def cola_ensemble_workspace_bytes(h):
+    n = ctypes.c_size_t()
+    _check(load_library().cola_ensemble_workspace_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def cola_ensemble_set_workspace(h, ws, stream=None):
+    _check(load_library().cola_ensemble_set_workspace(h, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def cola_ensemble_offsets(h, nbox):
+    poff = np.zeros(nbox + 1, dtype=np.int64)
+    moff = np.zeros(nbox + 1, dtype=np.int64)
+    _check(load_library().cola_ensemble_offsets(h, poff.ctypes.data_as(ctypes.c_void_p),
+                                                moff.ctypes.data_as(ctypes.c_void_p)))
+    return poff, moff
+
+
+def cola_ensemble_noise(h, seeds, noise, stream=None):
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check(load_library().cola_ensemble_noise(h, sd.ctypes.data_as(ctypes.c_void_p), _ptr(noise), _stream(stream)))
+
+
+def cola_ensemble_ic_2lpt(h, noise, s, v, s1, s2, stream=None):
+    _check(load_library().cola_ensemble_ic_2lpt(h, _ptr(noise), _ptr(s), _ptr(v), _ptr(s1), _ptr(s2),
+                                                _stream(stream)))
+
+
+def cola_ensemble_step(h, step, s, v, s1, s2, stream=None):
+    _check(load_library().cola_ensemble_step(h, int(step), _ptr(s), _ptr(v), _ptr(s1), _ptr(s2), _stream(stream)))
+
+
+def cola_ensemble_density(h, s, delta, stream=None):
+    _check(load_library().cola_ensemble_density(h, _ptr(s), _ptr(delta), _stream(stream)))
+
+
+def cola_ensemble_power(h, delta, nbins, k, pk, nmodes, stream=None):
+    _check(load_library().cola_ensemble_power(h, _ptr(delta), int(nbins), _ptr(k), _ptr(pk), _ptr(nmodes),
+                                              _stream(stream)))
+
+
+def cola_ensemble_tune(h, s, reps=3, stream=None):
+    best = cola_ensemble_tuning()
+    ms = np.zeros(COLA_ENSEMBLE_TUNE_CANDIDATES, dtype=np.float64)
+    _check(load_library().cola_ensemble_tune(h, _ptr(s), int(reps), ctypes.byref(best),
+                                             ms.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return best, ms
+
+
+def cola_ensemble_get_tuning(h):
+    t = cola_ensemble_tuning()
+    _check(load_library().cola_ensemble_get_tuning(h, ctypes.byref(t)))
+    return t
+
+
+def cola_ensemble_set_tuning(h, tuning, stream=None):
+    _check(load_library().cola_ensemble_set_tuning(h, ctypes.byref(tuning), _stream(stream)))
+
+
+def cola_ensemble_use_graphs(h, enable):
+    _check(load_library().cola_ensemble_use_graphs(h, int(bool(enable))))
+
+
+def cola_ensemble_status(h, stream=None):
+    _check(load_library().cola_ensemble_status(h, _stream(stream)))
+
+
 # ---- convenience wrapper ----------------------------------------------------------------------
 class Plan:
     """A COLA plan plus its device workspace (allocated with torch on ``device``)."""
@@ -298,6 +398,122 @@ class Plan:
         grad = self._empty(self.n3)
         cola_ic_2lpt_adjoint(self.handle, noise, lam_s, lam_s1, lam_s2, grad)
         return grad
+
+
+def _make_config(np_side, ng, box, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96, n_lpt=-2.5, nsteps=10,
+                 a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, adjoint=False):
+    cfg = cola_config_default()
+    cfg.np, cfg.ng, cfg.box = int(np_side), int(ng), float(box)
+    cfg.cosmo = cola_cosmo(omega_m, omega_l, h, sigma8, n_s)
+    cfg.n_lpt, cfg.nsteps, cfg.a_init, cfg.a_final = float(n_lpt), int(nsteps), float(a_init), float(a_final)
+    cfg.deconv, cfg.fixed_bits, cfg.adjoint = int(deconv), int(fixed_bits), int(bool(adjoint))
+    return cfg
+
+
+class Ensemble:
+    """Independent COLA boxes of different sizes evolved together (one launch per kernel class
+    per force evaluation, each step replayed from a CUDA graph).
+
+    ``boxes``: sequence of (np_side, ng, box) tuples or dicts of Plan keyword arguments.
+    Particle arrays are concatenated over boxes: a [3, n_total] tensor holds box b's SoA block
+    in its flat elements [3 poff[b], 3 poff[b+1]); ``split`` returns the per-box [3, np^3] views."""
+
+    def __init__(self, boxes, device="cuda", **common):
+        cfgs = []
+        for b in boxes:
+            kw = dict(common)
+            if isinstance(b, dict):
+                kw.update(b)
+            else:
+                kw.update(np_side=b[0], ng=b[1], box=b[2])
+            cfgs.append(_make_config(**kw))
+        self.cfgs = cfgs
+        self.nbox = len(cfgs)
+        self.nps = [int(c.np) for c in cfgs]
+        self.ngs = [int(c.ng) for c in cfgs]
+        self.nsteps = int(cfgs[0].nsteps)
+        self.device = torch.device(device)
+        self.handle = cola_ensemble_create(cfgs)
+        nbytes = cola_ensemble_workspace_bytes(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_view = self.workspace[off:off + nbytes]
+        cola_ensemble_set_workspace(self.handle, self._ws_view)
+        self.poff, self.moff = cola_ensemble_offsets(self.handle, self.nbox)
+        self.n_total = int(self.poff[-1])
+        self.cells_total = int(self.moff[-1])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.cola_ensemble_destroy(h)
+            self.handle = None
+
+    def _empty(self, shape, dtype=torch.float32):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def split(self, x):
+        """Per-box [3, np^3] views of a concatenated particle array."""
+        flat = x.reshape(-1)
+        return [flat[3 * self.poff[b]:3 * self.poff[b + 1]].view(3, -1) for b in range(self.nbox)]
+
+    def split_mesh(self, m):
+        return [m[self.moff[b]:self.moff[b + 1]] for b in range(self.nbox)]
+
+    def noise(self, seeds):
+        out = self._empty(self.n_total)
+        cola_ensemble_noise(self.handle, seeds, out)
+        return out
+
+    def ic_2lpt(self, noise):
+        _expect(noise, torch.float32, self.n_total, "noise")
+        s, v, s1, s2 = (self._empty(3 * self.n_total) for _ in range(4))
+        cola_ensemble_ic_2lpt(self.handle, noise, s, v, s1, s2)
+        return s, v, s1, s2
+
+    def step(self, i, s, v, s1, s2):
+        for t, n in ((s, "s"), (v, "v"), (s1, "s1"), (s2, "s2")):
+            _expect(t, torch.float32, 3 * self.n_total, n)
+        cola_ensemble_step(self.handle, i, s, v, s1, s2)
+
+    def run(self, noise):
+        s, v, s1, s2 = self.ic_2lpt(noise)
+        for i in range(self.nsteps + 1):
+            self.step(i, s, v, s1, s2)
+        return s, v, s1, s2
+
+    def density(self, s):
+        _expect(s, torch.float32, 3 * self.n_total, "s")
+        d = self._empty(self.cells_total)
+        cola_ensemble_density(self.handle, s, d)
+        return d
+
+    def power(self, delta, nbins):
+        _expect(delta, torch.float32, self.cells_total, "delta")
+        k = self._empty((self.nbox, nbins), torch.float64)
+        pk = self._empty((self.nbox, nbins), torch.float64)
+        nm = self._empty((self.nbox, nbins), torch.int64)
+        cola_ensemble_power(self.handle, delta, nbins, k, pk, nm)
+        return k, pk, nm
+
+    def tune(self, s, reps=3):
+        _expect(s, torch.float32, 3 * self.n_total, "s")
+        return cola_ensemble_tune(self.handle, s, reps)
+
+    @property
+    def tuning(self):
+        t = cola_ensemble_get_tuning(self.handle)
+        return (t.threads, t.tile_shape, t.blocks_per_sm)
+
+    @tuning.setter
+    def tuning(self, value):
+        cola_ensemble_set_tuning(self.handle, cola_ensemble_tuning(*value))
+
+    def use_graphs(self, enable):
+        cola_ensemble_use_graphs(self.handle, enable)
+
+    def status(self):
+        cola_ensemble_status(self.handle)
 
 
 class ColaDensity(torch.autograd.Function):

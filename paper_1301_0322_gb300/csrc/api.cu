@@ -47,7 +47,8 @@ static size_t layout(cola_plan* p, char* base) {
   const size_t region = off;
   const size_t half_g = sizeof(float2) * ng * ng * p->Pg;
   w.meshA = (float2*)take(half_g);
-  for (int j = 0; j < 3; ++j) w.meshG[j] = (float2*)take(half_g);
+  w.meshG[0] = nullptr;  // the x component is never stored as a half spectrum
+  for (int j = 1; j < 3; ++j) w.meshG[j] = (float2*)take(half_g);
   w.freal = (float*)take(sizeof(float) * 3 * ng3);
   const size_t pm_end = off;
   off = region;
@@ -86,6 +87,42 @@ static int force_meshes(cola_plan* p, const float* s, cudaStream_t st) {
   if (rc) return rc;
   return launch_force_passes(p->geo, p->tiles, s, w.idx, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
                              p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
+}
+
+}  // namespace cola
+
+namespace cola {
+int profile_read(Profiler& pr, int32_t max_entries, char* names, int64_t* launches, double* ms, int32_t* count) {
+  if (!names || !launches || !ms || !count || max_entries < 1) return fail(COLA_EINVAL, "null argument");
+  std::vector<std::string> keys;
+  std::vector<int64_t> n;
+  std::vector<double> t;
+  for (auto& r : pr.recs) {
+    COLA_CUDA_CHECK(cudaEventSynchronize(r.stop));
+    float el = 0.f;
+    COLA_CUDA_CHECK(cudaEventElapsedTime(&el, r.start, r.stop));
+    size_t i = 0;
+    while (i < keys.size() && keys[i] != r.name) ++i;
+    if (i == keys.size()) {
+      keys.emplace_back(r.name);
+      n.push_back(0);
+      t.push_back(0.0);
+    }
+    n[i] += 1;
+    t[i] += el;
+    pr.pool.push_back(r.start);
+    pr.pool.push_back(r.stop);
+  }
+  pr.recs.clear();
+  const int m = std::min<int>((int)keys.size(), max_entries);
+  for (int i = 0; i < m; ++i) {
+    std::memset(names + 64 * i, 0, 64);
+    std::strncpy(names + 64 * i, keys[i].c_str(), 63);
+    launches[i] = n[i];
+    ms[i] = t[i];
+  }
+  *count = m;
+  return COLA_OK;
 }
 
 }  // namespace cola
@@ -447,37 +484,8 @@ int cola_profile(cola_plan* plan, int32_t enable) {
 
 int cola_profile_read(cola_plan* plan, int32_t max_entries, char* names, int64_t* launches, double* ms,
                       int32_t* count) {
-  if (!plan || !names || !launches || !ms || !count || max_entries < 1) return fail(COLA_EINVAL, "null argument");
-  Profiler& pr = plan->prof;
-  std::vector<std::string> keys;
-  std::vector<int64_t> n;
-  std::vector<double> t;
-  for (auto& r : pr.recs) {
-    COLA_CUDA_CHECK(cudaEventSynchronize(r.stop));
-    float el = 0.f;
-    COLA_CUDA_CHECK(cudaEventElapsedTime(&el, r.start, r.stop));
-    size_t i = 0;
-    while (i < keys.size() && keys[i] != r.name) ++i;
-    if (i == keys.size()) {
-      keys.emplace_back(r.name);
-      n.push_back(0);
-      t.push_back(0.0);
-    }
-    n[i] += 1;
-    t[i] += el;
-    pr.pool.push_back(r.start);
-    pr.pool.push_back(r.stop);
-  }
-  pr.recs.clear();
-  const int m = std::min<int>((int)keys.size(), max_entries);
-  for (int i = 0; i < m; ++i) {
-    std::memset(names + 64 * i, 0, 64);
-    std::strncpy(names + 64 * i, keys[i].c_str(), 63);
-    launches[i] = n[i];
-    ms[i] = t[i];
-  }
-  *count = m;
-  return COLA_OK;
+  if (!plan) return fail(COLA_EINVAL, "null plan");
+  return profile_read(plan->prof, max_entries, names, launches, ms, count);
 }
 
 int cola_launch_count(uint64_t* count) {

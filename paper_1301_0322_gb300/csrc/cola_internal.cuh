@@ -51,7 +51,7 @@ struct Workspace {
   int* err = nullptr;       // latched error bits
   // PM step (aliases the IC region)
   float2* meshA = nullptr;  // half spectrum, ng x ng x Pg
-  float2* meshG[3] = {nullptr, nullptr, nullptr};
+  float2* meshG[3] = {nullptr, nullptr, nullptr};  // [1], [2]: y and z force half spectra ([0] unused)
   float* freal = nullptr;   // 3 x ng^3 force meshes (freal[0..ng^3) doubles as delta)
   // particle binning
   int* keys = nullptr;
@@ -95,6 +95,8 @@ namespace cola {
 // ---- host helpers (api.cu) ------------------------------------------------------------
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+struct Profiler;
+int profile_read(Profiler& pr, int32_t max_entries, char* names, int64_t* launches, double* ms, int32_t* count);
 bool fft_size_supported(int n);
 
 // ---- host coefficient module (coeffs.cpp) -----------------------------------------------

@@ -1,0 +1,792 @@
+// Ensembles of independent COLA boxes of different sizes (the many-realisation use of Sec. 1
+// and Sec. 4) evolved together: one launch per kernel class per force evaluation for all
+// boxes, each launch a persistent kernel whose blocks walk a work list of (box, item) pairs.
+//
+// Each box keeps a full single-box plan (its coefficient table, twiddles and mesh buffers);
+// the ensemble adds a description of every box for the device, the shared particle-sort
+// buffers and the work lists.  The bins of all boxes form one array (box b's bins start at
+// bin_base), so one scan serves every box, and box b's sorted particle indices land in
+// positions [poff[b], poff[b+1]) of the shared index array.
+//
+// One step (eq. ALCtimestep) = keys, 3 scan phases, scatter, deposit + x r2c, y pass, z pass
+// with the Green's function, inverse y passes, inverse x passes, gather + kick + drift:
+// 11 launches for the whole ensemble, recorded once per step as a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cola_internal.cuh"
+#include "particle_bodies.cuh"
+#include "pm_bodies.cuh"
+
+namespace cola {
+
+#define COLA_ENS_SIZES(X) X(64) X(96) X(128) X(192) X(256)
+
+// per-box description read by the ensemble kernels
+struct BoxDesc {
+  Geometry g;
+  Tiles tl;
+  int P, deconv, bin_base, pad_;
+  float kf, norm, dscale, pad2_;
+  int64_t pbase;            // first particle of the box in the ensemble arrays
+  float2* A;                // half spectrum [ng][ng][P]
+  float2* Gy;
+  float2* Gz;
+  float* F;                 // force meshes [3][ng^3]
+  const float2* tw;         // exp(-2 pi i m / ng)
+  const float* coef;        // (nsteps + 1) x kCoef32
+  int* err;
+};
+
+enum { kEParticles, kEDeposit, kECols, kEC2r, kENumLists };
+enum { kKKeys, kKScatter, kKDeposit, kKYfwd, kKZgreen, kKYinv, kKC2r, kKGather, kKNum };
+
+constexpr int kEnsMaxBoxes = 4096;
+
+namespace {
+
+// largest b with starts[b] <= item (starts ascending, starts[0] = 0)
+__device__ __forceinline__ int find_box(const int* __restrict__ starts, int nbox, int item) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(starts + mid) <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// rows of a deposit tile and its two shapes (tile_shape 0 / 1)
+__host__ __device__ constexpr int ens_tile_ty(int rows, int shape) {
+  return shape == 0 ? (rows == 16 ? 4 : 8) : (rows == 16 ? 8 : (rows == 32 ? 4 : 16));
+}
+
+// ---- persistent kernels -----------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_keys(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
+                                              int nbox, const float* __restrict__ s, int* __restrict__ keys,
+                                              int* __restrict__ counts) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    keys_body(d.g, d.tl, s + 3 * d.pbase, p, p < d.g.np3, d.bin_base, keys + d.pbase, counts, d.err);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
+                                                 int nbox, const int* __restrict__ keys, int* __restrict__ cursor,
+                                                 unsigned* __restrict__ idx) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    scatter_body(p, p < d.g.np3, keys + d.pbase, cursor, idx);
+  }
+}
+
+// One tile of one box.  Not inlined: every (size, tile) instantiation gets its own register
+// allocation instead of the union of all of them.
+template <int N, int TY, int TZ>
+__device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const float* __restrict__ s,
+                                          const unsigned* __restrict__ idx, const int* __restrict__ offsets,
+                                          int tile) {
+  extern __shared__ __align__(16) unsigned long long ens_smem[];
+  __shared__ int ints[28];
+  deposit_fftx_body<N, TY, TZ>(d->g, d->tl, s, idx, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile, ens_smem,
+                               ints);
+}
+
+template <int N, int NT>
+__device__ __forceinline__ void deposit_item(const BoxDesc* d, const float* s, const unsigned* idx,
+                                             const int* offsets, int tile) {
+  constexpr int ROWS = NT / FFTConf<N / 2>::T;
+  constexpr int TY0 = ens_tile_ty(ROWS, 0), TY1 = ens_tile_ty(ROWS, 1);
+  if (d->tl.ty == TY0)
+    deposit_tile<N, TY0, ROWS / TY0>(d, s, idx, offsets, tile);
+  else
+    deposit_tile<N, TY1, ROWS / TY1>(d, s, idx, offsets, tile);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __restrict__ boxes,
+                                                           const int* __restrict__ starts, int nbox,
+                                                           const float* __restrict__ s,
+                                                           const unsigned* __restrict__ idx,
+                                                           const int* __restrict__ offsets) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc* d = boxes + b;
+    const int local = item - __ldg(starts + b);
+    const float* sb = s + 3 * d->pbase;
+    const int* ob = offsets + d->bin_base;
+    switch (d->g.ng) {
+#define X(N)                                         \
+  case N:                                            \
+    deposit_item<N, NT>(d, sb, idx, ob, local);      \
+    break;
+      COLA_ENS_SIZES(X)
+#undef X
+      default:
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+// column passes: kind 0 = forward y, 1 = z with the Green's function, 2 = inverse y (three outputs)
+template <int NT, int KIND>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
+                                              int nbox) {
+  extern __shared__ __align__(16) unsigned long long ens_smem[];
+  float2* sm = reinterpret_cast<float2*>(ens_smem);
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int local = item - __ldg(starts + b);
+    switch (d.g.ng) {
+#define X(N)                                                                                              \
+  case N: {                                                                                               \
+    constexpr int W = NT / FFTConf<N>::T, nbx = (N / 2 + 1 + W - 1) / W;                                  \
+    const int bx = local % nbx, slab = local / nbx;                                                       \
+    if (KIND == 0)                                                                                        \
+      cols_body<N, W, false>(d.A, (int64_t)N * d.P, d.P, N / 2 + 1, d.tw, bx, slab, sm);                 \
+    else if (KIND == 1)                                                                                   \
+      z_green_body<N, W>(d.A, d.Gz, d.P, d.kf, d.deconv, d.norm, d.tw, bx, slab, sm);                     \
+    else                                                                                                  \
+      y_inv3_body<N, W>(d.A, d.Gy, d.Gz, d.P, d.kf, d.tw, bx, slab, sm);                                  \
+  } break;
+      COLA_ENS_SIZES(X)
+#undef X
+      default:
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
+                                              int nbox) {
+  extern __shared__ __align__(16) unsigned long long ens_smem[];
+  float2* sm = reinterpret_cast<float2*>(ens_smem);
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int local = item - __ldg(starts + b);
+    switch (d.g.ng) {
+#define X(N)                                                                       \
+  case N: {                                                                        \
+    constexpr int RB = NT / FFTConf<N / 2>::T, nrb = N * N / RB;                   \
+    c2r3_body<N, RB>(d.A, d.Gy, d.Gz, d.F, d.P, d.kf, d.tw, local % nrb, local / nrb, sm); \
+  } break;
+      COLA_ENS_SIZES(X)
+#undef X
+      default:
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
+                                                int nbox, float* __restrict__ s, float* __restrict__ v,
+                                                const float* __restrict__ s1, const float* __restrict__ s2, int step,
+                                                int mode) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    if (p < d.g.np3) {
+      const int64_t o = 3 * d.pbase;
+      gather_kick_drift_body(d.g, d.F, s + o, v + o, s1 + o, s2 + o, d.coef + (size_t)step * kCoef32, mode, nullptr,
+                             p);
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------------
+int host_T(int n) {
+  switch (n) {
+#define X(N) \
+  case N:    \
+    return FFTConf<N>::T;
+    X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+#undef X
+    default:
+      return 0;
+  }
+}
+
+bool ens_size_supported(int n) {
+  switch (n) {
+#define X(N) case N:
+    COLA_ENS_SIZES(X)
+#undef X
+    return true;
+    default:
+      return false;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Shape {
+  int W, nbx, RB, rows, ty, tz;
+};
+
+Shape box_shape(int n, int nt, int tile_shape) {
+  Shape s{};
+  s.W = nt / host_T(n);
+  s.nbx = (n / 2 + 1 + s.W - 1) / s.W;
+  s.RB = nt / host_T(n / 2);
+  s.rows = s.RB;
+  s.ty = ens_tile_ty(s.rows, tile_shape);
+  s.tz = s.rows / s.ty;
+  return s;
+}
+
+int xrow_ld_host(int m) { return ((m + 1 + ((m + 1) >> 3) + 1) + 15) / 16 * 16 + 8; }
+
+}  // namespace
+}  // namespace cola
+
+using namespace cola;
+
+struct cola_ensemble {
+  std::vector<cola_plan*> plans;
+  int nbox = 0, nsteps = 0, min_ng = 0;
+  std::vector<int64_t> poff, moff;
+  std::vector<size_t> plan_off;
+  size_t ens_off = 0, ws_bytes = 0;
+  int max_bins_total = 0;
+  void* ws_base = nullptr;
+  // shared device buffers
+  int* keys = nullptr;
+  unsigned* idx = nullptr;
+  int* counts = nullptr;
+  int* offsets = nullptr;
+  int* cursor = nullptr;
+  int* scan_blocks = nullptr;
+  BoxDesc* d_boxes = nullptr;
+  int* d_starts = nullptr;
+  // current launch configuration
+  cola_ensemble_tuning tuning{256, 0, 0};
+  std::vector<BoxDesc> h_boxes;
+  std::vector<int> h_starts;
+  int total_bins = 0;
+  int grid[kKNum] = {};
+  size_t smem[kKNum] = {};
+  int version = 0;
+  int num_sms = 0;
+  // graphs
+  bool use_graphs = true;
+  cudaStream_t cap = nullptr;
+  struct Cached {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int version = -1;
+    unsigned long long kernels = 0;
+  };
+  std::vector<Cached> graphs;
+  Profiler prof;
+
+  ~cola_ensemble() {
+    for (auto& c : graphs)
+      if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (cap) cudaStreamDestroy(cap);
+    for (auto* p : plans) cola_plan_destroy(p);
+  }
+};
+
+namespace cola {
+namespace {
+
+template <int NT>
+int kernel_attrs(cola_ensemble* e) {
+  const void* fns[kKNum] = {(const void*)ke_keys<NT>,    (const void*)ke_scatter<NT>, (const void*)ke_deposit<NT>,
+                            (const void*)ke_cols<NT, 0>, (const void*)ke_cols<NT, 1>, (const void*)ke_cols<NT, 2>,
+                            (const void*)ke_c2r3<NT>,    (const void*)ke_gather<NT>};
+  const int lists[kKNum] = {kEParticles, kEParticles, kEDeposit, kECols, kECols, kECols, kEC2r, kEParticles};
+  for (int k = 0; k < kKNum; ++k) {
+    if (e->smem[k] > 227 * 1024) return fail(COLA_EUNSUPPORTED, "ensemble kernel: shared memory request too large");
+    COLA_CUDA_CHECK(cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem[k]));
+    int occ = 0;
+    COLA_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[k], NT, e->smem[k]));
+    if (occ < 1) return fail(COLA_EUNSUPPORTED, "ensemble kernel does not fit on an SM");
+    const int per_sm = e->tuning.blocks_per_sm > 0 ? std::min(occ, (int)e->tuning.blocks_per_sm) : occ;
+    const int items = e->h_starts[(size_t)lists[k] * (e->nbox + 1) + e->nbox];
+    e->grid[k] = std::max(1, std::min(items, per_sm * e->num_sms));
+  }
+  return COLA_OK;
+}
+
+// (re)build the box descriptions, work lists and launch shapes for e->tuning
+int configure(cola_ensemble* e, cudaStream_t st) {
+  const int nt = e->tuning.threads;
+  const int nb = e->nbox;
+  e->h_boxes.assign(nb, BoxDesc{});
+  e->h_starts.assign((size_t)kENumLists * (nb + 1), 0);
+  std::fill(e->smem, e->smem + kKNum, (size_t)0);
+  int bins = 0;
+  for (int b = 0; b < nb; ++b) {
+    cola_plan* p = e->plans[b];
+    const int n = p->geo.ng;
+    const Shape sh = box_shape(n, nt, e->tuning.tile_shape);
+    BoxDesc& d = e->h_boxes[b];
+    d.g = p->geo;
+    d.tl.ty = sh.ty;
+    d.tl.tz = sh.tz;
+    d.tl.nty = n / sh.ty;
+    d.tl.ntz = n / sh.tz;
+    d.tl.nbins = d.tl.nty * d.tl.ntz * 4;
+    d.P = p->Pg;
+    d.deconv = p->cfg.deconv;
+    d.bin_base = bins;
+    bins += d.tl.nbins;
+    d.kf = (float)(2.0 * 3.14159265358979323846 / p->cfg.box);
+    d.norm = (float)(1.0 / ((double)n * n * n));
+    d.dscale = (float)((double)n * n * n / ((double)p->geo.np3 * std::ldexp(1.0, 3 * p->geo.fbits)));
+    d.pbase = e->poff[b];
+    d.A = p->ws.meshA;
+    d.Gy = p->ws.meshG[1];
+    d.Gz = p->ws.meshG[2];
+    d.F = p->ws.freal;
+    d.tw = p->ws.tw_g;
+    d.coef = p->ws.coef;
+    d.err = p->ws.err;
+    const int64_t part_items = (p->geo.np3 + nt - 1) / nt;
+    const int64_t items[kENumLists] = {part_items, (int64_t)d.tl.nty * d.tl.ntz, (int64_t)sh.nbx * n,
+                                       (int64_t)n * n / sh.RB * 3};
+    for (int l = 0; l < kENumLists; ++l) {
+      int* st_l = &e->h_starts[(size_t)l * (nb + 1)];
+      const int64_t next = (int64_t)st_l[b] + items[l];
+      if (next > 0x7fffffff) return fail(COLA_EINVAL, "ensemble: too many work items");
+      st_l[b + 1] = (int)next;
+    }
+    const int M = n / 2;
+    const size_t dep = sizeof(unsigned long long) * sh.rows * std::max(n, xrow_ld_host(M));
+    const size_t cols = sizeof(float2) * n * sh.W;
+    const size_t c2r = sizeof(float2) * sh.RB * xrow_ld_host(M);
+    e->smem[kKDeposit] = std::max(e->smem[kKDeposit], dep);
+    e->smem[kKYfwd] = std::max(e->smem[kKYfwd], cols);
+    e->smem[kKZgreen] = std::max(e->smem[kKZgreen], 2 * cols);
+    e->smem[kKYinv] = std::max(e->smem[kKYinv], 2 * cols);
+    e->smem[kKC2r] = std::max(e->smem[kKC2r], c2r);
+  }
+  if (bins > e->max_bins_total) return fail(COLA_EINVAL, "ensemble: bin count above the workspace sizing");
+  e->total_bins = bins;
+  int rc = nt == 128 ? kernel_attrs<128>(e) : kernel_attrs<256>(e);
+  if (rc) return rc;
+  if (e->ws_base) {
+    COLA_CUDA_CHECK(cudaMemcpyAsync(e->d_boxes, e->h_boxes.data(), sizeof(BoxDesc) * nb, cudaMemcpyHostToDevice, st));
+    COLA_CUDA_CHECK(cudaMemcpyAsync(e->d_starts, e->h_starts.data(), sizeof(int) * e->h_starts.size(),
+                                    cudaMemcpyHostToDevice, st));
+    // the pageable source vectors may change before an asynchronous copy reads them
+    COLA_CUDA_CHECK(cudaStreamSynchronize(st));
+  }
+  ++e->version;
+  return COLA_OK;
+}
+
+template <int NT>
+int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
+  const int nb = e->nbox;
+  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
+  const int* sd = e->d_starts + (size_t)kEDeposit * (nb + 1);
+  const int* sc = e->d_starts + (size_t)kECols * (nb + 1);
+  const int* sr = e->d_starts + (size_t)kEC2r * (nb + 1);
+  {
+    LaunchScope ls_("ens_keys", st);
+    ke_keys<NT><<<e->grid[kKKeys], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->counts);
+  }
+  COLA_LAUNCH_CHECK();
+  Tiles all{};
+  all.nbins = e->total_bins;
+  int rc = launch_scan(all, e->counts, e->offsets, e->cursor, e->scan_blocks, st);
+  if (rc) return rc;
+  {
+    LaunchScope ls_("ens_scatter", st);
+    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, e->keys, e->cursor, e->idx);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_deposit_fftx", st);
+    ke_deposit<NT><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, s, e->idx, e->offsets);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_fft_y", st);
+    ke_cols<NT, 0><<<e->grid[kKYfwd], NT, e->smem[kKYfwd], st>>>(e->d_boxes, sc, nb);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_fft_z_green", st);
+    ke_cols<NT, 1><<<e->grid[kKZgreen], NT, e->smem[kKZgreen], st>>>(e->d_boxes, sc, nb);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_fft_y_inv3", st);
+    ke_cols<NT, 2><<<e->grid[kKYinv], NT, e->smem[kKYinv], st>>>(e->d_boxes, sc, nb);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_fft_x_c2r3", st);
+    ke_c2r3<NT><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb);
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+template <int NT>
+int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1, const float* s2, cudaStream_t st) {
+  int rc = enqueue_mesh_passes<NT>(e, s, st);
+  if (rc) return rc;
+  const int nb = e->nbox;
+  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
+  const int mode = step == e->nsteps ? 1 : 0;
+  {
+    LaunchScope ls_("ens_gather_kick_drift", st);
+    ke_gather<NT><<<e->grid[kKGather], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int enqueue_step_any(cola_ensemble* e, int step, float* s, float* v, const float* s1, const float* s2,
+                     cudaStream_t st) {
+  return e->tuning.threads == 128 ? enqueue_step<128>(e, step, s, v, s1, s2, st)
+                                  : enqueue_step<256>(e, step, s, v, s1, s2, st);
+}
+
+int enqueue_mesh_any(cola_ensemble* e, const float* s, cudaStream_t st) {
+  return e->tuning.threads == 128 ? enqueue_mesh_passes<128>(e, s, st) : enqueue_mesh_passes<256>(e, s, st);
+}
+
+int check_ens(const cola_ensemble* e) {
+  if (!e) return fail(COLA_EINVAL, "null ensemble");
+  if (!e->ws_base) return fail(COLA_ENOWORKSPACE, "cola_ensemble_set_workspace has not been called");
+  return COLA_OK;
+}
+
+bool valid_tuning(const cola_ensemble_tuning& t) {
+  return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) && t.blocks_per_sm >= 0 &&
+         t.blocks_per_sm <= 64;
+}
+
+}  // namespace
+}  // namespace cola
+
+extern "C" {
+
+int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out) {
+  if (!boxes || !out) return fail(COLA_EINVAL, "null argument");
+  *out = nullptr;
+  if (nbox < 1 || nbox > kEnsMaxBoxes) return fail(COLA_EINVAL, "nbox must be in [1, 4096]");
+  for (int b = 0; b < nbox; ++b) {
+    if (!ens_size_supported((int)boxes[b].ng))
+      return fail(COLA_EUNSUPPORTED, "ensemble boxes need ng in {64, 96, 128, 192, 256} (box " + std::to_string(b) +
+                                         ")");
+    if (boxes[b].nsteps != boxes[0].nsteps) return fail(COLA_EINVAL, "every ensemble box needs the same nsteps");
+    if (boxes[b].adjoint) return fail(COLA_EINVAL, "ensemble boxes do not carry adjoint buffers");
+  }
+  cola_ensemble* e = new cola_ensemble();
+  e->nbox = nbox;
+  e->nsteps = boxes[0].nsteps;
+  e->poff.assign(nbox + 1, 0);
+  e->moff.assign(nbox + 1, 0);
+  e->plan_off.assign(nbox, 0);
+  size_t off = 0;
+  int64_t max_bins = 0;
+  e->min_ng = (int)boxes[0].ng;
+  for (int b = 0; b < nbox; ++b) {
+    cola_plan* p = nullptr;
+    int rc = cola_plan_create(&boxes[b], &p);
+    if (rc) {
+      const std::string why = std::string("ensemble box ") + std::to_string(b) + ": " + cola_last_error();
+      delete e;
+      return fail(rc, why);
+    }
+    e->plans.push_back(p);
+    e->poff[b + 1] = e->poff[b] + p->geo.np3;
+    e->moff[b + 1] = e->moff[b] + p->ng3;
+    e->plan_off[b] = off;
+    off += align256(p->ws_bytes);
+    e->min_ng = std::min(e->min_ng, p->geo.ng);
+    // most bins over the candidate launch shapes: the fewest tile rows (128 threads)
+    const int n = p->geo.ng;
+    const int rows = 128 / host_T(n / 2);
+    max_bins += 4LL * n * n / rows;
+  }
+  if (e->poff[nbox] >= 0x7fffffffLL || max_bins >= 0x7fffffffLL) {
+    delete e;
+    return fail(COLA_EINVAL, "ensemble: more than 2^31 particles or bins");
+  }
+  e->max_bins_total = (int)max_bins;
+  e->ens_off = off;
+  const int64_t np_all = e->poff[nbox];
+  Tiles all{};
+  all.nbins = e->max_bins_total;
+  off += align256(sizeof(int) * np_all);                   // keys
+  off += align256(sizeof(unsigned) * np_all);              // idx
+  off += align256(sizeof(int) * all.nbins);                // counts
+  off += align256(sizeof(int) * (all.nbins + 1));          // offsets
+  off += align256(sizeof(int) * all.nbins);                // cursor
+  off += align256(sizeof(int) * scan_block_count(all));    // scan block sums
+  off += align256(sizeof(BoxDesc) * nbox);                 // box descriptions
+  off += align256(sizeof(int) * kENumLists * (nbox + 1));  // work lists
+  e->ws_bytes = off;
+  e->graphs.resize(e->nsteps + 1);
+  *out = e;
+  return COLA_OK;
+}
+
+int cola_ensemble_destroy(cola_ensemble* ens) {
+  delete ens;
+  return COLA_OK;
+}
+
+int cola_ensemble_workspace_bytes(const cola_ensemble* ens, size_t* bytes) {
+  if (!ens || !bytes) return fail(COLA_EINVAL, "null argument");
+  *bytes = ens->ws_bytes;
+  return COLA_OK;
+}
+
+int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes, cola_stream stream) {
+  if (!ens || !dev_ptr) return fail(COLA_EINVAL, "null argument");
+  if (bytes < ens->ws_bytes) return fail(COLA_EINVAL, "workspace too small");
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(COLA_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)dev_ptr;
+  for (int b = 0; b < ens->nbox; ++b) {
+    cola_plan* p = ens->plans[b];
+    const int rc = cola_set_workspace(p, base + ens->plan_off[b], p->ws_bytes, stream);
+    if (rc) return rc;
+  }
+  size_t off = ens->ens_off;
+  auto take = [&](size_t n) {
+    char* ptr = base + off;
+    off += align256(n);
+    return ptr;
+  };
+  const int64_t np_all = ens->poff[ens->nbox];
+  Tiles all{};
+  all.nbins = ens->max_bins_total;
+  ens->keys = (int*)take(sizeof(int) * np_all);
+  ens->idx = (unsigned*)take(sizeof(unsigned) * np_all);
+  ens->counts = (int*)take(sizeof(int) * all.nbins);
+  ens->offsets = (int*)take(sizeof(int) * (all.nbins + 1));
+  ens->cursor = (int*)take(sizeof(int) * all.nbins);
+  ens->scan_blocks = (int*)take(sizeof(int) * scan_block_count(all));
+  ens->d_boxes = (BoxDesc*)take(sizeof(BoxDesc) * ens->nbox);
+  ens->d_starts = (int*)take(sizeof(int) * kENumLists * (ens->nbox + 1));
+  COLA_CUDA_CHECK(cudaMemsetAsync(ens->counts, 0, sizeof(int) * all.nbins, st));
+  int dev = 0;
+  COLA_CUDA_CHECK(cudaGetDevice(&dev));
+  COLA_CUDA_CHECK(cudaDeviceGetAttribute(&ens->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!ens->cap) COLA_CUDA_CHECK(cudaStreamCreateWithFlags(&ens->cap, cudaStreamNonBlocking));
+  ens->ws_base = dev_ptr;
+  return configure(ens, st);
+}
+
+int cola_ensemble_offsets(const cola_ensemble* ens, int64_t* poff, int64_t* moff) {
+  if (!ens || !poff || !moff) return fail(COLA_EINVAL, "null argument");
+  std::memcpy(poff, ens->poff.data(), sizeof(int64_t) * ens->poff.size());
+  std::memcpy(moff, ens->moff.data(), sizeof(int64_t) * ens->moff.size());
+  return COLA_OK;
+}
+
+int cola_ensemble_noise(cola_ensemble* ens, const uint64_t* seeds, float* noise, cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!seeds || !noise) return fail(COLA_EINVAL, "null array");
+  for (int b = 0; b < ens->nbox; ++b)
+    if ((rc = cola_noise(ens->plans[b], seeds[b], noise + ens->poff[b], stream))) return rc;
+  return COLA_OK;
+}
+
+int cola_ensemble_ic_2lpt(cola_ensemble* ens, const float* noise, float* s, float* v, float* s1, float* s2,
+                          cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!noise || !s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
+  for (int b = 0; b < ens->nbox; ++b) {
+    const int64_t o = ens->poff[b], o3 = 3 * ens->poff[b];
+    if ((rc = cola_ic_2lpt(ens->plans[b], noise + o, s + o3, v + o3, s1 + o3, s2 + o3, stream))) return rc;
+  }
+  return COLA_OK;
+}
+
+int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, const float* s1, const float* s2,
+                       cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
+  if (step < 0 || step > ens->nsteps) return fail(COLA_EINVAL, "step out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ens->use_graphs || ens->prof.on) {
+    ProfilerGuard pg(&ens->prof);
+    return enqueue_step_any(ens, step, s, v, s1, s2, st);
+  }
+  auto& c = ens->graphs[step];
+  const void* key[4] = {s, v, s1, s2};
+  if (!c.exec || c.version != ens->version || std::memcmp(c.key, key, sizeof(key)) != 0) {
+    if (c.exec) {
+      COLA_CUDA_CHECK(cudaGraphExecDestroy(c.exec));
+      c.exec = nullptr;
+    }
+    ProfilerGuard pg(nullptr);
+    const unsigned long long before = g_launches.load();
+    COLA_CUDA_CHECK(cudaStreamBeginCapture(ens->cap, cudaStreamCaptureModeRelaxed));
+    rc = enqueue_step_any(ens, step, s, v, s1, s2, ens->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ens->cap, &graph);
+    const unsigned long long kernels = g_launches.load() - before;
+    g_launches.fetch_sub(kernels);  // counted when the graph runs
+    if (rc || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc ? rc : fail(COLA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&c.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      c.exec = nullptr;
+      return fail(COLA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    std::memcpy(c.key, key, sizeof(key));
+    c.version = ens->version;
+    c.kernels = kernels;
+  }
+  COLA_CUDA_CHECK(cudaGraphLaunch(c.exec, st));
+  g_launches.fetch_add(c.kernels);
+  return COLA_OK;
+}
+
+int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!s || !delta) return fail(COLA_EINVAL, "null array");
+  for (int b = 0; b < ens->nbox; ++b)
+    if ((rc = cola_density(ens->plans[b], s + 3 * ens->poff[b], nullptr, delta + ens->moff[b], stream))) return rc;
+  return COLA_OK;
+}
+
+int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
+                        int64_t* nmodes, cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!delta || !k || !pk || !nmodes) return fail(COLA_EINVAL, "null array");
+  if (nbins < 1 || nbins > ens->min_ng) return fail(COLA_EINVAL, "nbins must be in [1, smallest ng]");
+  for (int b = 0; b < ens->nbox; ++b) {
+    const size_t o = (size_t)b * nbins;
+    if ((rc = cola_power(ens->plans[b], delta + ens->moff[b], nbins, k + o, pk + o, nmodes + o, stream))) return rc;
+  }
+  return COLA_OK;
+}
+
+int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning) {
+  if (!ens || !tuning) return fail(COLA_EINVAL, "null argument");
+  *tuning = ens->tuning;
+  return COLA_OK;
+}
+
+int cola_ensemble_set_tuning(cola_ensemble* ens, const cola_ensemble_tuning* tuning, cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape 0 or 1");
+  const cola_ensemble_tuning old = ens->tuning;
+  ens->tuning = *tuning;
+  if ((rc = configure(ens, (cudaStream_t)stream))) {
+    ens->tuning = old;
+    configure(ens, (cudaStream_t)stream);
+    return rc;
+  }
+  return COLA_OK;
+}
+
+int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
+                       cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  if (!s) return fail(COLA_EINVAL, "null array");
+  if (reps < 1 || reps > 1000) return fail(COLA_EINVAL, "reps must be in [1, 1000]");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  COLA_CUDA_CHECK(cudaEventCreate(&e0));
+  COLA_CUDA_CHECK(cudaEventCreate(&e1));
+  const cola_ensemble_tuning start = ens->tuning;
+  cola_ensemble_tuning winner = start;
+  double best_ms = 1e300;
+  ProfilerGuard pg(nullptr);
+  for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
+    ens->tuning = cola_ensemble_tuning{(i & 4) ? 256 : 128, (i >> 1) & 1, (i & 1) ? 2 : 0};
+    if ((rc = configure(ens, st))) break;
+    if ((rc = enqueue_mesh_any(ens, s, st))) break;  // warm-up
+    if (cudaEventRecord(e0, st) != cudaSuccess) {
+      rc = fail(COLA_ECUDA, "event record");
+      break;
+    }
+    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_mesh_any(ens, s, st);
+    if (rc) break;
+    float el = 0.f;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
+      rc = fail(COLA_ECUDA, "event timing");
+      break;
+    }
+    const double t = (double)el / reps;
+    if (ms) ms[i] = t;
+    if (t < best_ms) {
+      best_ms = t;
+      winner = ens->tuning;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ens->tuning = rc ? start : winner;
+  const int rc2 = configure(ens, st);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (best) *best = ens->tuning;
+  return COLA_OK;
+}
+
+int cola_ensemble_use_graphs(cola_ensemble* ens, int32_t enable) {
+  if (!ens) return fail(COLA_EINVAL, "null ensemble");
+  ens->use_graphs = enable != 0;
+  return COLA_OK;
+}
+
+int cola_ensemble_status(cola_ensemble* ens, cola_stream stream) {
+  int rc = check_ens(ens);
+  if (rc) return rc;
+  for (int b = 0; b < ens->nbox; ++b)
+    if ((rc = cola_status(ens->plans[b], stream)))
+      return fail(rc, std::string("ensemble box ") + std::to_string(b) + ": " + cola_last_error());
+  return COLA_OK;
+}
+
+int cola_ensemble_profile(cola_ensemble* ens, int32_t enable) {
+  if (!ens) return fail(COLA_EINVAL, "null ensemble");
+  ens->prof.on = enable != 0;
+  return COLA_OK;
+}
+
+int cola_ensemble_profile_read(cola_ensemble* ens, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                               int32_t* count) {
+  if (!ens) return fail(COLA_EINVAL, "null ensemble");
+  return profile_read(ens->prof, max_entries, names, launches, ms, count);
+}
+
+}  // extern "C"

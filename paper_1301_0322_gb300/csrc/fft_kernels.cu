@@ -5,6 +5,7 @@
 // z pass (strided complex columns, in place).  The c2r runs the same passes in reverse.
 #include "cola_internal.cuh"
 #include "fft.cuh"
+#include "pm_bodies.cuh"
 
 namespace cola {
 
@@ -26,18 +27,8 @@ template <int N, bool INV>
 __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
     k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols,
                const float2* __restrict__ tw) {
-  constexpr int W = col_width<N>();
   extern __shared__ float2 smem[];
-  const int w = threadIdx.x % W, t = threadIdx.x / W;
-  const int col = blockIdx.x * W + w;
-  const bool valid = col < ncols;
-  float2* base = data + (int64_t)blockIdx.y * slab_stride + (valid ? col : 0);
-  auto load = [&](int n) -> float2 { return valid ? base[(int64_t)n * row_stride] : make_float2(0.f, 0.f); };
-  auto mem = [&](int n) -> float2& { return smem[n * W + w]; };
-  auto store = [&](int n, float2 x) {
-    if (valid) base[(int64_t)n * row_stride] = x;
-  };
-  fft_1d<N, 1, INV>(t, tw, load, mem, store);
+  cols_body<N, col_width<N>(), INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
 }
 
 // Real rows of length N -> half-spectrum rows (N/2 + 1 entries, stride P), via a complex

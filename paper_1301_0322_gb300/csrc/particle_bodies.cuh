@@ -1,0 +1,120 @@
+// Per-particle device bodies of a COLA force evaluation (Sec. 2 PM code; App. A.3 eq. KDKALC),
+// shared by the single-box kernels and the multi-box (ensemble) kernels.  Every body handles
+// the one particle p of the calling thread; keys_body and scatter_body use warp-wide votes and
+// must be called by all 32 lanes of a warp (live marks the lanes that own a particle).
+#pragma once
+#include "cola_internal.cuh"
+#include "pm_common.cuh"
+
+namespace cola {
+
+// key = ((tz_tile * nty) + ty_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
+// is the last row of its tile along y (z): its cloud also reaches the next tile.
+__device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
+  const int ty = cy / tl.ty, tz = cz / tl.tz;
+  const int ry = (cy - ty * tl.ty == tl.ty - 1) ? 1 : 0;
+  const int rz = (cz - tz * tl.tz == tl.tz - 1) ? 2 : 0;
+  return (tz * tl.nty + ty) * 4 + ry + rz;
+}
+
+// Bin key of particle p (plus bin_base) into keys[p]; counts[key] += 1 with one atomic per
+// distinct key in the warp.  s is the box's SoA [3][np^3] displacement.
+__device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s, int64_t p,
+                                          bool live, int bin_base, int* __restrict__ keys, int* __restrict__ counts,
+                                          int* __restrict__ err) {
+  int key = -1;
+  if (live) {
+    int ix, iy, iz;
+    lattice_index(g, p, ix, iy, iz);
+    const float sy = s[g.np3 + p], sz = s[2 * g.np3 + p];
+    if (!isfinite(s[p]) || !isfinite(sy) || !isfinite(sz)) atomicOr(err, kErrNonFinite);
+    int cy, ty, cz, tz;
+    fixed_axis(g, iy, sy, cy, ty);
+    fixed_axis(g, iz, sz, cz, tz);
+    key = bin_base + tile_key(tl, cy, cz);
+    keys[p] = key;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+}
+
+// Counting-sort scatter: idx[cursor[keys[p]]++] = p, one atomic per distinct key in the warp.
+__device__ __forceinline__ void scatter_body(int64_t p, bool live, const int* __restrict__ keys,
+                                             int* __restrict__ cursor, unsigned* __restrict__ idx) {
+  const int key = live ? keys[p] : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (live) idx[base + rank] = (unsigned)p;
+}
+
+// CIC gather of the three force meshes fmesh [3][ng^3] at particle p (the deposit's weights),
+// then (mode 0) Kick + Drift of eq. KDKALC, (mode 1) the final Kick + L+ of eq. Lops, or
+// (mode 2) the gathered force alone into gout [3][np^3].
+__device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const float* __restrict__ fmesh,
+                                                       float* __restrict__ s, float* __restrict__ v,
+                                                       const float* __restrict__ s1, const float* __restrict__ s2,
+                                                       const float* __restrict__ coef, int mode,
+                                                       float* __restrict__ gout, int64_t p) {
+  const int64_t n3 = g.np3;
+  const int ng = g.ng;
+  const int64_t ng3 = (int64_t)ng * ng * ng;
+  int ix, iy, iz;
+  lattice_index(g, p, ix, iy, iz);
+  const float sp[3] = {s[p], s[n3 + p], s[2 * n3 + p]};
+  int c[3], t[3];
+  fixed_axis(g, ix, sp[0], c[0], t[0]);
+  fixed_axis(g, iy, sp[1], c[1], t[1]);
+  fixed_axis(g, iz, sp[2], c[2], t[2]);
+  const float inv_one = 1.0f / (float)(1 << g.fbits);
+  float w1[3], w0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    w1[d] = (float)t[d] * inv_one;  // exact
+    w0[d] = 1.0f - w1[d];           // exact
+  }
+  const int xs[2] = {c[0], wrap_inc(c[0], ng)};
+  const int ys[2] = {c[1], wrap_inc(c[1], ng)};
+  const int zs[2] = {c[2], wrap_inc(c[2], ng)};
+  float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const float wzy = (dz ? w1[2] : w0[2]) * (dy ? w1[1] : w0[1]);
+      const int64_t row = ((int64_t)zs[dz] * ng + ys[dy]) * ng;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const float w = wzy * (dx ? w1[0] : w0[0]);
+        const int64_t gi = row + xs[dx];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f[j] = fmaf(w, __ldg(fmesh + j * ng3 + gi), f[j]);
+      }
+    }
+  if (mode == 2) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gout[j * n3 + p] = f[j];
+    return;
+  }
+  const float cKF = __ldg(coef + kCKF), cK1 = __ldg(coef + kCK1), cK2 = __ldg(coef + kCK2);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float a1 = s1[j * n3 + p], a2 = s2[j * n3 + p];
+    float vj = v[j * n3 + p];
+    vj += cKF * f[j] - cK1 * a1 - cK2 * a2;  // Kick (eq. KDKALC)
+    if (mode == 0) {
+      const float sj = sp[j] + __ldg(coef + kCD) * vj + __ldg(coef + kDD1) * a1 + __ldg(coef + kDD2) * a2;  // Drift
+      s[j * n3 + p] = sj;
+    } else {
+      vj += __ldg(coef + kTD1) * a1 + __ldg(coef + kTD2) * a2;  // L+ (eq. Lops)
+    }
+    v[j * n3 + p] = vj;
+  }
+}
+
+}  // namespace cola

@@ -1,0 +1,313 @@
+// Device bodies of the mesh passes, shared by the single-box kernels and the multi-box
+// (ensemble) kernels.  Each body processes one block's share of work given by explicit block
+// indices and shared-memory pointers, so that a persistent kernel can run the bodies of
+// different boxes (and mesh sizes) one after another.
+#pragma once
+#include "cola_internal.cuh"
+#include "fft.cuh"
+#include "pm_common.cuh"
+
+namespace cola {
+
+// ---- helpers -----------------------------------------------------------------------------
+__device__ __forceinline__ float sinc_pi_f(int n, int ng) {
+  if (n == 0) return 1.0f;
+  const float x = (float)n / (float)ng;
+  return sinpif(x) / (3.14159265358979323846f * x);
+}
+__device__ __forceinline__ int signed_mode(int k, int n) { return k < n / 2 ? k : k - n; }
+
+// first-derivative factor i k_j (zero on the Nyquist plane |n_j| = N/2)
+__device__ __forceinline__ float2 mul_ik(float2 a, float k) { return make_float2(-k * a.y, k * a.x); }
+
+
+template <int N>
+__host__ __device__ constexpr int green_width() {
+  return FFTConf<N>::T * 16 <= 256 ? 16 : (FFTConf<N>::T * 8 <= 256 ? 8 : (FFTConf<N>::T * 4 <= 512 ? 4 : 2));
+}
+
+// block (bx, slab): W columns of one slab of the in-place strided FFT (T(N) * W threads);
+// smem: N W float2.  Element (n, col) at data[slab * slab_stride + n * row_stride + col].
+template <int N, int W, bool INV>
+__device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride,
+                                          int ncols, const float2* __restrict__ tw, int bx, int slab, float2* smem) {
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int col = bx * W + w;
+  const bool valid = col < ncols;
+  float2* base = data + (int64_t)slab * slab_stride + (valid ? col : 0);
+  auto load = [&](int n) -> float2 { return valid ? base[(int64_t)n * row_stride] : make_float2(0.f, 0.f); };
+  auto mem = [&](int n) -> float2& { return smem[n * W + w]; };
+  auto store = [&](int n, float2 x) {
+    if (valid) base[(int64_t)n * row_stride] = x;
+  };
+  fft_1d<N, 1, INV>(t, tw, load, mem, store);
+}
+
+// ---- 1. deposit + x r2c -----------------------------------------------------------------------
+// block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
+// bytes of shared memory; ints: 28 ints of shared memory
+template <int N, int TY, int TZ>
+__device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s,
+                                                  const unsigned* __restrict__ idx, const int* __restrict__ offsets,
+                                                  float2* __restrict__ out, int P, const float2* __restrict__ tw,
+                                                  float dscale, int* __restrict__ err, int tile,
+                                                  unsigned long long* acc, int* ints) {
+  constexpr int M = N / 2, T = FFTConf<M>::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS;
+  int* rbeg = ints;
+  int* rpre = ints + 9;
+  int* rlen = ints + 19;
+  const int tyi = tile % tl.nty, tzi = tile / tl.nty;
+  const int y0 = tyi * TY, z0 = tzi * TZ;
+  for (int i = threadIdx.x; i < ROWS * N; i += NT) acc[i] = 0ull;
+  // the tile's own 4 bins and the boundary bins of its 3 lower neighbours, loaded in parallel
+  if (threadIdx.x < 9) {
+    const int k = threadIdx.x;
+    const int tym = tyi == 0 ? tl.nty - 1 : tyi - 1;
+    const int tzm = tzi == 0 ? tl.ntz - 1 : tzi - 1;
+    const int ty_ = (k == 4 || k == 5 || k == 8) ? tym : tyi;
+    const int tz_ = k >= 6 ? tzm : tzi;
+    const int reg = k < 4 ? k : ((k == 4 || k == 5) ? (k == 4 ? 1 : 3) : (k == 6 ? 2 : 3));
+    const int b = (tz_ * tl.nty + ty_) * 4 + reg;
+    const int o0 = offsets[b];
+    rbeg[k] = o0;
+    rlen[k] = offsets[b + 1] - o0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < 9; ++k) {
+      rpre[k] = run;
+      run += rlen[k];
+    }
+    rpre[9] = run;
+  }
+  __syncthreads();
+  const int total = rpre[9];
+  const unsigned long long one = 1ull << g.fbits;
+  constexpr int U = 4;  // particles in flight per thread
+  for (int base = threadIdx.x; base < total; base += NT * U) {
+    int64_t pp[U];
+    float sv[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * NT;
+      pp[u] = -1;
+      if (i < total) {
+        int r = 0;
+#pragma unroll
+        for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
+        pp[u] = idx[rbeg[r] + (i - rpre[r])];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (pp[u] >= 0) {
+        sv[u][0] = s[pp[u]];
+        sv[u][1] = s[g.np3 + pp[u]];
+        sv[u][2] = s[2 * g.np3 + pp[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pp[u] < 0) continue;
+      int ix, iy, iz;
+      lattice_index(g, pp[u], ix, iy, iz);
+      int cx, tx, cy, ty, cz, tz;
+      fixed_axis(g, ix, sv[u][0], cx, tx);
+      fixed_axis(g, iy, sv[u][1], cy, ty);
+      fixed_axis(g, iz, sv[u][2], cz, tz);
+      const int cx1 = wrap_inc(cx, N);
+      const unsigned long long wx0 = one - tx, wx1 = tx;
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const int lz = (dz ? wrap_inc(cz, N) : cz) - z0;
+        if (lz < 0 || lz >= TZ) continue;
+        const unsigned long long wz = dz ? (unsigned long long)tz : one - tz;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int ly = (dy ? wrap_inc(cy, N) : cy) - y0;
+          if (ly < 0 || ly >= TY) continue;
+          const unsigned long long wzy = wz * (dy ? (unsigned long long)ty : one - ty);
+          unsigned long long* row = acc + (lz * TY + ly) * N;
+          atomicAdd(row + cx, wzy * wx0);
+          atomicAdd(row + cx1, wzy * wx1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // real-to-complex FFT of each tile row; z[n] = (delta[2n], delta[2n+1])
+  const int t = threadIdx.x % T, w = threadIdx.x / T;
+  const unsigned long long* arow = acc + w * N;
+  float2* buf = reinterpret_cast<float2*>(acc) + w * LD;
+  bool overflow = false;
+  auto load = [&](int n) -> float2 {
+    const unsigned long long a = arow[2 * n], b = arow[2 * n + 1];
+    overflow |= ((a | b) >> 62) != 0ull;
+    return make_float2(fmaf(__ull2float_rn(a), dscale, -1.0f), fmaf(__ull2float_rn(b), dscale, -1.0f));
+  };
+  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
+  auto store = [&](int n, float2 x) { buf[xpad(n)] = x; };
+  fft_1d<M, 2, false>(t, tw, load, mem, store);
+  if (overflow) atomicOr(err, kErrOverflow);
+  __syncthreads();
+  const int lz = w / TY, ly = w - lz * TY;
+  float2* dst = out + ((int64_t)(z0 + lz) * N + (y0 + ly)) * P;
+  for (int k = t; k <= M; k += T) {
+    const float2 a = buf[xpad(k == M ? 0 : k)];
+    const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
+    const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+    const float2 d = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
+    dst[k] = c_add(e, c_mul(__ldg(tw + k), make_float2(d.y, -d.x)));
+  }
+}
+
+// ---- 3. z pass with the Green's function ------------------------------------------------------------
+// block (bx, ky): W columns kx of the slab ky (T(N) * W threads); sm: 2 N W float2
+template <int N, int W>
+__device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __restrict__ Gz, int P, float kf,
+                                             int deconv, float norm, const float2* __restrict__ tw, int bx, int ky,
+                                             float2* sm) {
+  constexpr int nh = N / 2 + 1, NT = FFTConf<N>::T * W;
+  float2* S0 = sm;           // delta_k of the slab, [n][W]
+  float2* S1 = sm + N * W;   // exchange buffer
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = bx * W + w;
+  const bool valid = kx < nh;
+  const int64_t zstride = (int64_t)N * P;
+  float2* a = A + (int64_t)ky * P + (valid ? kx : 0);
+  float2* gz = Gz + (int64_t)ky * P + (valid ? kx : 0);
+  auto mem = [&](int n) -> float2& { return S1[n * W + w]; };
+  {
+    auto load = [&](int n) -> float2 { return valid ? a[n * zstride] : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) { S0[n * W + w] = x; };
+    fft_1d<N, 1, false>(t, tw, load, mem, store);
+  }
+  // sinc^2 table of the z index, then phi_k = delta_k g(k) in place in S0 (one pass)
+  float* sz2 = reinterpret_cast<float*>(S1);  // S1 is free between the transforms
+  for (int n = threadIdx.x; n < N; n += NT) {
+    const float sz = sinc_pi_f(signed_mode(n, N), N);
+    sz2[n] = sz * sz;
+  }
+  __syncthreads();
+  {
+    const int ny = signed_mode(ky, N);
+    const float sy = sinc_pi_f(ny, N);
+    const float wy = sy * sy;
+    for (int i = threadIdx.x; i < N * W; i += NT) {
+      const int n = i / W, c = i - n * W;
+      const int nx = bx * W + c;
+      const int nz = signed_mode(n, N);
+      const int m2 = nx * nx + ny * ny + nz * nz;
+      float gk = 0.0f;
+      if (m2 != 0 && nx < nh) {
+        gk = norm / (kf * kf * (float)m2);
+        if (deconv) {
+          const float sx = sinc_pi_f(nx, N);
+          const float wk = (sx * sx) * wy * sz2[n];
+          gk /= (deconv == 2 ? wk * wk : wk);
+        }
+      }
+      S0[i] = c_scale(S0[i], gk);
+    }
+  }
+  __syncthreads();
+  {
+    auto load = [&](int n) -> float2 { return S0[n * W + w]; };
+    auto store = [&](int n, float2 x) {
+      if (valid) a[n * zstride] = x;
+    };
+    fft_1d<N, 1, true>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 {
+      const float kz = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
+      return mul_ik(S0[n * W + w], kz);
+    };
+    auto store = [&](int n, float2 x) {
+      if (valid) gz[n * zstride] = x;
+    };
+    fft_1d<N, 1, true>(t, tw, load, mem, store);
+  }
+}
+
+// ---- 4. inverse y passes ------------------------------------------------------------------------------------
+// block (bx, z): W columns kx of the slab z (T(N) * W threads); sm: 2 N W float2
+template <int N, int W>
+__device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz,
+                                            int P, float kf, const float2* __restrict__ tw, int bx, int z,
+                                            float2* sm) {
+  constexpr int nh = N / 2 + 1, T = FFTConf<N>::T;
+  float2* S0 = sm;
+  float2* S1 = sm + N * W;
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = bx * W + w;
+  const bool valid = kx < nh;
+  const int64_t slab = (int64_t)z * N * P + (valid ? kx : 0);
+  float2* b = B + slab;
+  float2* gy = Gy + slab;
+  float2* gz = Gz + slab;
+  for (int n = t; n < N; n += T) S0[n * W + w] = valid ? b[(int64_t)n * P] : make_float2(0.f, 0.f);
+  __syncthreads();
+  auto mem = [&](int n) -> float2& { return S1[n * W + w]; };
+  {
+    auto load = [&](int n) -> float2 { return S0[n * W + w]; };
+    auto store = [&](int n, float2 x) {
+      if (valid) b[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 {
+      const float ky = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
+      return mul_ik(S0[n * W + w], ky);
+    };
+    auto store = [&](int n, float2 x) {
+      if (valid) gy[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 { return valid ? gz[(int64_t)n * P] : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) {
+      if (valid) gz[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true>(t, tw, load, mem, store);
+  }
+}
+
+// ---- 5. inverse x passes of the three components -------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int c2r3_rows() {
+  return FFTConf<N / 2>::T >= 256 ? 1 : 256 / FFTConf<N / 2>::T;
+}
+
+// block (bx, comp): RB rows of one force component (T(N/2) * RB threads); smem: RB LD float2
+template <int N, int RB>
+__device__ __forceinline__ void c2r3_body(const float2* __restrict__ C, const float2* __restrict__ Gy,
+                                          const float2* __restrict__ Gz, float* __restrict__ F, int P, float kf,
+                                          const float2* __restrict__ tw, int bx, int comp, float2* smem) {
+  constexpr int M = N / 2, T = FFTConf<M>::T, LD = xrow_ld<M>();
+  const float2* srcm = comp == 0 ? C : (comp == 1 ? Gy : Gz);
+  const int t = threadIdx.x % T, w = threadIdx.x / T;
+  const int64_t row = (int64_t)bx * RB + w;
+  const float2* src = srcm + row * P;
+  float2* buf = smem + w * LD;
+  for (int k = t; k <= M; k += T) {
+    float2 x = src[k];
+    if (comp == 0) x = mul_ik(x, k == M ? 0.0f : kf * (float)k);
+    buf[xpad(k)] = x;
+  }
+  __syncthreads();
+  auto load = [&](int n) -> float2 {
+    const float2 a = buf[xpad(n)], bb = c_conj(buf[xpad(M - n)]);
+    const float2 e = c_add(a, bb);
+    const float2 o = c_mul(c_sub(a, bb), c_conj(__ldg(tw + n)));
+    return make_float2(e.x - o.y, e.y + o.x);
+  };
+  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
+  float2* dst = reinterpret_cast<float2*>(F + (int64_t)comp * N * N * N + row * N);
+  auto store = [&](int n, float2 x) { dst[n] = x; };
+  fft_1d<M, 2, true>(t, tw, load, mem, store);
+}
+
+}  // namespace cola

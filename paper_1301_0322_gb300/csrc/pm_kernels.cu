@@ -8,39 +8,15 @@
 //              Drift (or the final L+ of eq. Lops)
 #include "cola_internal.cuh"
 #include "pm_common.cuh"
+#include "particle_bodies.cuh"
 
 namespace cola {
 
 // ---- binning -------------------------------------------------------------------------------
-// key = ((tz_tile * nty) + ty_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
-// is the last row of its tile along y (z): its cloud also reaches the next tile.
-__device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
-  const int ty = cy / tl.ty, tz = cz / tl.tz;
-  const int ry = (cy - ty * tl.ty == tl.ty - 1) ? 1 : 0;
-  const int rz = (cz - tz * tl.tz == tl.tz - 1) ? 2 : 0;
-  return (tz * tl.nty + ty) * 4 + ry + rz;
-}
-
 __global__ void k_keys(Geometry g, Tiles tl, const float* __restrict__ s, int* __restrict__ keys,
                        int* __restrict__ counts, int* __restrict__ err) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = p < g.np3;
-  int key = -1;
-  if (live) {
-    int ix, iy, iz;
-    lattice_index(g, p, ix, iy, iz);
-    const float sy = s[g.np3 + p], sz = s[2 * g.np3 + p];
-    if (!isfinite(s[p]) || !isfinite(sy) || !isfinite(sz)) atomicOr(err, kErrNonFinite);
-    int cy, ty, cz, tz;
-    fixed_axis(g, iy, sy, cy, ty);
-    fixed_axis(g, iz, sz, cz, tz);
-    key = tile_key(tl, cy, cz);
-    keys[p] = key;
-  }
-  // one atomic per distinct key in the warp
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int lane = threadIdx.x & 31;
-  if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+  keys_body(g, tl, s, p, p < g.np3, 0, keys, counts, err);
 }
 
 // Exclusive scan of the bin counts in three launches (block sums, scan of the block sums,
@@ -110,16 +86,7 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ co
 __global__ void k_scatter(int64_t np3, const int* __restrict__ keys, int* __restrict__ cursor,
                           unsigned* __restrict__ idx) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = p < np3;
-  const int key = live ? keys[p] : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  const int rank = __popc(peers & ((1u << lane) - 1u));
-  if (live) idx[base + rank] = (unsigned)p;
+  scatter_body(p, p < np3, keys, cursor, idx);
 }
 
 // ---- deposit ----------------------------------------------------------------------------------
@@ -251,61 +218,7 @@ __global__ void __launch_bounds__(256) k_gather_kick_drift(Geometry g, const flo
                                                             const float* __restrict__ coef, int mode,
                                                             float* __restrict__ gout) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.np3) return;
-  const int64_t n3 = g.np3;
-  const int ng = g.ng;
-  const int64_t ng3 = (int64_t)ng * ng * ng;
-  int ix, iy, iz;
-  lattice_index(g, p, ix, iy, iz);
-  const float sp[3] = {s[p], s[n3 + p], s[2 * n3 + p]};
-  int c[3], t[3];
-  fixed_axis(g, ix, sp[0], c[0], t[0]);
-  fixed_axis(g, iy, sp[1], c[1], t[1]);
-  fixed_axis(g, iz, sp[2], c[2], t[2]);
-  const float inv_one = 1.0f / (float)(1 << g.fbits);
-  float w1[3], w0[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    w1[d] = (float)t[d] * inv_one;  // exact
-    w0[d] = 1.0f - w1[d];           // exact
-  }
-  const int xs[2] = {c[0], wrap_inc(c[0], ng)};
-  const int ys[2] = {c[1], wrap_inc(c[1], ng)};
-  const int zs[2] = {c[2], wrap_inc(c[2], ng)};
-  float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const float wzy = (dz ? w1[2] : w0[2]) * (dy ? w1[1] : w0[1]);
-      const int64_t row = ((int64_t)zs[dz] * ng + ys[dy]) * ng;
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const float w = wzy * (dx ? w1[0] : w0[0]);
-        const int64_t gi = row + xs[dx];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) f[j] = fmaf(w, __ldg(fmesh + j * ng3 + gi), f[j]);
-      }
-    }
-  if (mode == 2) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gout[j * n3 + p] = f[j];
-    return;
-  }
-  const float cKF = __ldg(coef + kCKF), cK1 = __ldg(coef + kCK1), cK2 = __ldg(coef + kCK2);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const float a1 = s1[j * n3 + p], a2 = s2[j * n3 + p];
-    float vj = v[j * n3 + p];
-    vj += cKF * f[j] - cK1 * a1 - cK2 * a2;  // Kick (eq. KDKALC)
-    if (mode == 0) {
-      const float sj = sp[j] + __ldg(coef + kCD) * vj + __ldg(coef + kDD1) * a1 + __ldg(coef + kDD2) * a2;  // Drift
-      s[j * n3 + p] = sj;
-    } else {
-      vj += __ldg(coef + kTD1) * a1 + __ldg(coef + kTD2) * a2;  // L+ (eq. Lops)
-    }
-    v[j * n3 + p] = vj;
-  }
+  if (p < g.np3) gather_kick_drift_body(g, fmesh, s, v, s1, s2, coef, mode, gout, p);
 }
 
 // ---- launchers ------------------------------------------------------------------------------------

@@ -18,6 +18,11 @@ WORKLOADS = {
 }
 COSMOLOGY = dict(omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96)
 
+# the mock ensemble: 48 independent boxes of three sizes, all with 0.78 Mpc/h mesh cells;
+# (np, ng, box [Mpc/h]) per box in order, Philox seeds 100..147
+ENSEMBLE_48 = [(64, 128, 100.0)] * 16 + [(96, 192, 150.0)] * 16 + [(128, 256, 200.0)] * 16
+ENSEMBLE_48_SEEDS = list(range(100, 148))
+
 
 def gaussian_noise(n, seed):
     """Unit-variance white noise on the n^3 lattice, float32, shape (n^3,) in [iz][iy][ix] order."""

@@ -97,3 +97,33 @@ def test_host_coefficients_match_oracle(lib, om, ol, n_lpt, nsteps):
             assert row[6] == pytest.approx(g["D1"][i + 1] - g["D1"][i], rel=1e-8)
             assert row[7] == pytest.approx(g["D2"][i + 1] - g["D2"][i], rel=1e-7)
         assert row[15] == pytest.approx(g["d2u1"], rel=1e-9)
+
+
+def test_ensemble_create_validates_and_lays_out_the_boxes(lib):
+    def cfg(n_p, ng, nsteps=10):
+        c = lib.cola_config_default()
+        c.np, c.ng, c.nsteps = n_p, ng, nsteps
+        return c
+
+    h = lib.cola_ensemble_create([cfg(32, 64), cfg(48, 96), cfg(64, 256)])
+    try:
+        assert lib.cola_ensemble_workspace_bytes(h) > 0
+        poff, moff = lib.cola_ensemble_offsets(h, 3)
+        assert list(poff) == [0, 32**3, 32**3 + 48**3, 32**3 + 48**3 + 64**3]
+        assert list(moff) == [0, 64**3, 64**3 + 96**3, 64**3 + 96**3 + 256**3]
+        cdll = lib.load_library()
+        assert cdll.cola_ensemble_step(h, 0, None, None, None, None, None) == 5  # COLA_ENOWORKSPACE
+        t = lib.cola_ensemble_get_tuning(h)
+        assert (t.threads, t.tile_shape, t.blocks_per_sm) == (256, 0, 0)
+    finally:
+        lib.cola_ensemble_destroy(h)
+    with pytest.raises(lib.ColaError) as e:
+        lib.cola_ensemble_create([cfg(32, 64), cfg(32, 64, nsteps=5)])
+    assert e.value.code == 1
+    for bad_ng in (48, 384):
+        with pytest.raises(lib.ColaError) as e:
+            lib.cola_ensemble_create([cfg(32, 64), cfg(32, bad_ng)])
+        assert e.value.code == 4 and b"box 1" in lib.load_library().cola_last_error()
+    with pytest.raises(lib.ColaError) as e:
+        lib.cola_ensemble_create([])
+    assert e.value.code == 1
