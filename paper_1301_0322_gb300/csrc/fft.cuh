@@ -15,13 +15,16 @@
 
 namespace cola {
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex arithmetic with every rounding spelled out (__fadd_rn / __fmul_rn are never fused
+// into an FMA by the compiler): a kernel body then rounds identically in every kernel it is
+// inlined into, so the single-box and the ensemble kernels give bit-identical results.
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  return make_float2(fmaf(a.x, b.x, __fmul_rn(-a.y, b.y)), fmaf(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
 // multiply by -i (forward sign) or +i (inverse sign)
 template <bool INV>
 __device__ __forceinline__ float2 c_rot(float2 a) {

@@ -101,17 +101,18 @@ __device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const 
     for (int j = 0; j < 3; ++j) gout[j * n3 + p] = f[j];
     return;
   }
+  // explicit FMA chains: the same rounding in every kernel this body is inlined into
   const float cKF = __ldg(coef + kCKF), cK1 = __ldg(coef + kCK1), cK2 = __ldg(coef + kCK2);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const float a1 = s1[j * n3 + p], a2 = s2[j * n3 + p];
     float vj = v[j * n3 + p];
-    vj += cKF * f[j] - cK1 * a1 - cK2 * a2;  // Kick (eq. KDKALC)
+    vj = __fadd_rn(vj, fmaf(cKF, f[j], fmaf(-cK1, a1, __fmul_rn(-cK2, a2))));  // Kick (eq. KDKALC)
     if (mode == 0) {
-      const float sj = sp[j] + __ldg(coef + kCD) * vj + __ldg(coef + kDD1) * a1 + __ldg(coef + kDD2) * a2;  // Drift
-      s[j * n3 + p] = sj;
+      const float dj = fmaf(__ldg(coef + kCD), vj, fmaf(__ldg(coef + kDD1), a1, __fmul_rn(__ldg(coef + kDD2), a2)));
+      s[j * n3 + p] = __fadd_rn(sp[j], dj);  // Drift
     } else {
-      vj += __ldg(coef + kTD1) * a1 + __ldg(coef + kTD2) * a2;  // L+ (eq. Lops)
+      vj = __fadd_rn(vj, fmaf(__ldg(coef + kTD1), a1, __fmul_rn(__ldg(coef + kTD2), a2)));  // L+ (eq. Lops)
     }
     v[j * n3 + p] = vj;
   }

@@ -18,7 +18,7 @@ __device__ __forceinline__ float sinc_pi_f(int n, int ng) {
 __device__ __forceinline__ int signed_mode(int k, int n) { return k < n / 2 ? k : k - n; }
 
 // first-derivative factor i k_j (zero on the Nyquist plane |n_j| = N/2)
-__device__ __forceinline__ float2 mul_ik(float2 a, float k) { return make_float2(-k * a.y, k * a.x); }
+__device__ __forceinline__ float2 mul_ik(float2 a, float k) { return make_float2(__fmul_rn(-k, a.y), __fmul_rn(k, a.x)); }
 
 
 template <int N>
@@ -155,8 +155,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   for (int k = t; k <= M; k += T) {
     const float2 a = buf[xpad(k == M ? 0 : k)];
     const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
-    const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
-    const float2 d = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
+    const float2 e = c_scale(c_add(a, b), 0.5f);
+    const float2 d = c_scale(c_sub(a, b), 0.5f);
     dst[k] = c_add(e, c_mul(__ldg(tw + k), make_float2(d.y, -d.x)));
   }
 }
@@ -302,7 +302,7 @@ __device__ __forceinline__ void c2r3_body(const float2* __restrict__ C, const fl
     const float2 a = buf[xpad(n)], bb = c_conj(buf[xpad(M - n)]);
     const float2 e = c_add(a, bb);
     const float2 o = c_mul(c_sub(a, bb), c_conj(__ldg(tw + n)));
-    return make_float2(e.x - o.y, e.y + o.x);
+    return make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
   };
   auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
   float2* dst = reinterpret_cast<float2*>(F + (int64_t)comp * N * N * N + row * N);
