@@ -177,3 +177,57 @@ def unit_force_particles(pos, n_particles, ng, box, deconv=1):
     delta = overdensity(cic_deposit(pos, ng, box), n_particles)
     meshes = unit_force_mesh(delta, box, deconv)
     return np.stack([cic_gather(m, pos, box) for m in meshes])
+
+
+def unit_force_axis_wave(s_line, axis, n_p, ng, box, deconv=1):
+    """Unit force (the force mesh and gather above) on a lattice displaced along one axis only.
+
+    Special case used where the mesh is too large for unit_force_particles: every particle
+    (ix, iy, iz) is displaced by s_line[i_axis] along `axis` and not at all across it, and the
+    mesh side is an integer multiple r = ng / n_p of the lattice side.  Then the particles of
+    one lattice plane i_axis form a sheet sitting exactly on the mesh nodes c = 0 mod r of the
+    two transverse axes, and the same PM definition reduces to one dimension:
+
+      * deposit: rho(x, y, z) = rho_1(x) E(y) E(z), rho_1 the 1-D CIC deposit of the n_p sheet
+        positions (one unit each) and E(c) = [c = 0 mod r] = (1/r) sum_j exp(2 pi i j c / r);
+        so delta = r rho_1 sum_{j,l} exp(2 pi i (j y + l z) / r) - 1 and delta_1 = r rho_1 - 1;
+      * every transverse pair (j, l) carries the same x spectrum delta_1k for k_x != 0, at
+        transverse mode numbers (j ng / r, l ng / r);
+      * on the sheets (y, z = 0 mod r) all transverse phases are 1, the CIC gather is 1-D, and
+        g_axis(k_x) = i k_x delta_1k / W(k_x)^p * sum_{j,l} 1 / (W_j^p W_l^p (k_x^2 + k_j^2 + k_l^2)),
+        with the Nyquist plane of the component and k = 0 set to zero as in unit_force_mesh;
+      * the transverse components vanish: their gradient factor is zero at transverse mode 0
+        and on the Nyquist plane, and the sum over j (and over l) of i k_j cancels in pairs
+        (+-j) for the other modes.
+
+    s_line: displacements of the n_p sheets (float64 values of the float32 inputs), shape (n_p,).
+    Returns the axis component of g at each sheet, shape (n_p,), float64."""
+    r = ng // n_p
+    assert r * n_p == ng, "the mesh side must be a multiple of the lattice side"
+    x = np.mod(np.arange(n_p) * (box / n_p) + np.asarray(s_line, dtype=np.float64), box)
+    u = x * (ng / box)
+    base = np.floor(u).astype(np.int64)
+    frac = u - np.floor(u)
+    rho1 = np.zeros(ng)
+    np.add.at(rho1, base % ng, 1.0 - frac)
+    np.add.at(rho1, (base + 1) % ng, frac)
+    delta1 = r * rho1 - 1.0
+    dk = np.fft.rfft(delta1)
+    kf = 2.0 * np.pi / box
+    nx = np.arange(ng // 2 + 1)
+    kx = kf * nx
+    w1 = np.sinc(nx / ng) ** 2
+    trans = [((j * ng // r + ng // 2) % ng) - ng // 2 for j in range(r)]  # signed mode numbers
+    green = np.zeros(nx.size)
+    for j in trans:
+        for l in trans:
+            wt = (np.sinc(j / ng) ** 2 * np.sinc(l / ng) ** 2) ** deconv
+            k2 = kx**2 + (kf * j) ** 2 + (kf * l) ** 2
+            with np.errstate(divide="ignore"):
+                green += np.where(k2 > 0, 1.0 / (wt * k2), 0.0)
+    grad = np.where(nx == ng // 2, 0.0, kx)
+    gk = 1j * grad * dk * green / (w1**deconv)
+    gk[0] = 0.0
+    g = np.fft.irfft(gk, n=ng)
+    # 1-D CIC gather at the sheets
+    return g[base % ng] * (1.0 - frac) + g[(base + 1) % ng] * frac

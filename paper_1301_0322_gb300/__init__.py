@@ -5,10 +5,18 @@ from .cola import (COLA_NCOEF, ColaDensity, ColaError, Ensemble, Plan, cola_coef
                    cola_density_adjoint, cola_density_from_noise, cola_fft_r2c, cola_force, cola_ic_2lpt,
                    cola_ic_2lpt_adjoint, cola_noise, cola_plan_create, cola_plan_destroy, cola_power,
                    cola_power_noalloc, cola_set_workspace, cola_status, cola_step, cola_step_adjoint,
-                   cola_workspace_bytes, load_library)
+                   cola_workspace_bytes, load_library, cola_ensemble_create, cola_ensemble_destroy,
+                   cola_ensemble_workspace_bytes, cola_ensemble_set_workspace, cola_ensemble_offsets,
+                   cola_ensemble_noise, cola_ensemble_ic_2lpt, cola_ensemble_step, cola_ensemble_density,
+                   cola_ensemble_power, cola_ensemble_tune, cola_ensemble_get_tuning, cola_ensemble_set_tuning,
+                   cola_ensemble_use_graphs, cola_ensemble_status)
 
 __all__ = ["Plan", "Ensemble", "ColaError", "ColaDensity", "COLA_NCOEF", "load_library", "cola_config_default",
            "cola_plan_create", "cola_plan_destroy", "cola_workspace_bytes", "cola_set_workspace", "cola_coeffs",
            "cola_noise", "cola_ic_2lpt", "cola_step", "cola_force", "cola_density", "cola_power", "cola_fft_r2c",
            "cola_status", "cola_step_adjoint", "cola_density_adjoint", "cola_ic_2lpt_adjoint",
-           "cola_density_from_noise", "cola_power_noalloc"]
+           "cola_density_from_noise", "cola_power_noalloc", "cola_ensemble_create", "cola_ensemble_destroy",
+           "cola_ensemble_workspace_bytes", "cola_ensemble_set_workspace", "cola_ensemble_offsets",
+           "cola_ensemble_noise", "cola_ensemble_ic_2lpt", "cola_ensemble_step", "cola_ensemble_density",
+           "cola_ensemble_power", "cola_ensemble_tune", "cola_ensemble_get_tuning", "cola_ensemble_set_tuning",
+           "cola_ensemble_use_graphs", "cola_ensemble_status"]

@@ -157,3 +157,22 @@ def test_momentum_conservation_and_no_self_force(deconv):
     pair = rng.uniform(0, box, size=(3, 2))
     g2 = mesh.unit_force_particles(pair, 2, ng, box, deconv)
     assert np.allclose(g2[:, 0], -g2[:, 1], atol=1e-13)
+
+
+@pytest.mark.parametrize("n_p,ng,box,axis,m", [(16, 32, 50.0, 0, 1), (16, 32, 50.0, 1, 2), (12, 36, 40.0, 2, 1),
+                                               (8, 32, 30.0, 0, 3)])
+@pytest.mark.parametrize("deconv", [0, 1, 2])
+def test_axis_wave_reduction_equals_the_3d_force(n_p, ng, box, axis, m, deconv):
+    # the one-dimensional reduction of the PM force for a lattice displaced along one axis
+    # (mesh side r * lattice side) against the brute three-dimensional deposit/FFT/gather
+    k = 2 * np.pi * m / box
+    line = (0.4 / k * np.sin(k * np.arange(n_p) * box / n_p)).astype(np.float32).astype(np.float64)
+    q = mesh.lattice_q(n_p, box)
+    idx = mesh.lattice_index(n_p)[axis]
+    s = np.zeros_like(q)
+    s[axis] = line[idx]
+    g = mesh.unit_force_particles(np.mod(q + s, box), n_p**3, ng, box, deconv)
+    ref = mesh.unit_force_axis_wave(line, axis, n_p, ng, box, deconv)
+    scale = np.abs(ref).max()
+    assert np.abs(g[axis] - ref[idx]).max() <= 1e-12 * scale
+    assert np.abs(np.delete(g, axis, 0)).max() <= 1e-12 * scale
