@@ -43,6 +43,7 @@ extern "C" {
 #define COLA_EOVERFLOW 3       /* a device check failed (fixed-point overflow, non-finite) */
 #define COLA_EUNSUPPORTED 4    /* mesh or lattice size without an FFT kernel               */
 #define COLA_ENOWORKSPACE 5    /* cola_set_workspace has not been called                   */
+#define COLA_ETIMEOUT 6        /* a kernel's bounded wait on its asynchronous copies ran out */
 
 #define COLA_NCOEF 16 /* columns of the cola_coeffs table */
 
@@ -172,7 +173,8 @@ int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, do
 int cola_fft_r2c(cola_plan* plan, int32_t which, const float* in, float* out, cola_stream stream);
 
 /* Synchronise `stream` and report errors latched by kernels since the last call
- * (COLA_EOVERFLOW for a fixed-point overflow or a non-finite position), then clear them. */
+ * (COLA_EOVERFLOW for a fixed-point overflow or a non-finite position, COLA_ETIMEOUT if a
+ * kernel stopped waiting for its bulk copies), then clear them. */
 int cola_status(cola_plan* plan, cola_stream stream);
 
 /* cola_power without a plan, a workspace or any device allocation.  The paper has no

@@ -29,8 +29,9 @@ namespace cola {
 struct BoxDesc {
   Geometry g;
   Tiles tl;
-  int P, deconv, bin_base, pad_;
-  float kf, norm, dscale, pad2_;
+  int P, deconv, bin_base, c2r_rb;  // c2r_rb: rows per inverse-x work item
+  float kf, norm, dscale;
+  int c2r_ld;                        // row pitch (complex) of the staged inverse-x rows
   int64_t pbase;            // first particle of the box in the ensemble arrays
   float2* A;                // half spectrum [ng][ng][P]
   float2* Gy;
@@ -173,21 +174,55 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
   }
 }
 
+// Inverse x passes of all boxes: persistent, with the bulk copy of the next item (which may
+// belong to another box and mesh size) in flight during the transform of the current one.
+// half: float2 capacity of each of the two stage buffers.
 template <int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
-                                              int nbox) {
-  extern __shared__ __align__(16) unsigned long long ens_smem[];
+__global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restrict__ boxes,
+                                                        const int* __restrict__ starts, int nbox, int half,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned long long ens_smem[];
   float2* sm = reinterpret_cast<float2*>(ens_smem);
+  __shared__ __align__(8) uint64_t bars[2];
   const int total = __ldg(starts + nbox);
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int item, int buf) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int local = item - __ldg(starts + b);
+    const int rb = d.c2r_rb, n = d.g.ng;
+    const int nrb = n * n / rb;
+    const int comp = local / nrb;
+    const float2* m = comp == 0 ? d.A : (comp == 1 ? d.Gy : d.Gz);
+    c2r3_issue(sm + buf * half, m + (int64_t)(local - comp * nrb) * rb * d.P, rb, d.P, d.c2r_ld, &bars[buf]);
+  };
+  int item = blockIdx.x;
+  if (item < total && threadIdx.x < 32) issue(item, 0);
+  for (int it = 0; item < total; ++it, item += gridDim.x) {
+    const int buf = it & 1;
+    const int next = item + gridDim.x;
+    if (next < total && threadIdx.x < 32) issue(next, buf ^ 1);
+    const bool ok = mbar_wait(&bars[buf], (it >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+      if (next < total) mbar_wait(&bars[buf ^ 1], ((it + 1) >> 1) & 1);
+      return;
+    }
     const int b = find_box(starts, nbox, item);
     const BoxDesc& d = boxes[b];
     const int local = item - __ldg(starts + b);
     switch (d.g.ng) {
-#define X(N)                                                                       \
-  case N: {                                                                        \
-    constexpr int RB = NT / FFTConf<N / 2>::T, nrb = N * N / RB;                   \
-    c2r3_body<N, RB>(d.A, d.Gy, d.Gz, d.F, d.P, d.kf, d.tw, local % nrb, local / nrb, sm); \
+#define X(N)                                                                                       \
+  case N: {                                                                                        \
+    constexpr int RB = NT / FFTConf<N / 2>::T, nrb = N * N / RB;                                   \
+    const int comp = local / nrb;                                                                  \
+    c2r3_compute<N, RB>(sm + buf * half, d.F + (int64_t)comp * N * N * N + (int64_t)(local - comp * nrb) * RB * N, \
+                        comp, d.kf, d.tw);                                                         \
   } break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -378,7 +413,9 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     const int M = n / 2;
     const size_t dep = sizeof(unsigned long long) * sh.rows * std::max(n, xrow_ld_host(M));
     const size_t cols = sizeof(float2) * n * sh.W;
-    const size_t c2r = sizeof(float2) * sh.RB * xrow_ld_host(M);
+    d.c2r_rb = sh.RB;
+    d.c2r_ld = xrow_ld_host(M);
+    const size_t c2r = sizeof(float2) * 2 * sh.RB * xrow_ld_host(M);  // two stage buffers
     e->smem[kKDeposit] = std::max(e->smem[kKDeposit], dep);
     e->smem[kKYfwd] = std::max(e->smem[kKYfwd], cols);
     e->smem[kKZgreen] = std::max(e->smem[kKZgreen], 2 * cols);
@@ -443,7 +480,8 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_x_c2r3", st);
-    ke_c2r3<NT><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb);
+    const int half = (int)(e->smem[kKC2r] / (2 * sizeof(float2)));
+    ke_c2r3<NT><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb, half, e->plans[0]->ws.err);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;

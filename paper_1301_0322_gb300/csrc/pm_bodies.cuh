@@ -6,6 +6,7 @@
 #include "cola_internal.cuh"
 #include "fft.cuh"
 #include "pm_common.cuh"
+#include "tma.cuh"
 
 namespace cola {
 
@@ -276,36 +277,46 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
 }
 
 // ---- 5. inverse x passes of the three components -------------------------------------------------------------
+// Work item: RB consecutive rows of one component (C, Gy or Gz; P complex per row).  The rows
+// arrive in shared memory by bulk copy (TMA) at pitch LD = xrow_ld(N/2) while the block
+// computes the previous item; the first FFT stage reads them there, and later stages reuse
+// the same rows as their exchange buffer (the first stage has read all its inputs by then).
 template <int N>
 __host__ __device__ constexpr int c2r3_rows() {
-  return FFTConf<N / 2>::T >= 256 ? 1 : 256 / FFTConf<N / 2>::T;
+  return FFTConf<N / 2>::T >= 128 ? 1 : 128 / FFTConf<N / 2>::T;
 }
 
-// block (bx, comp): RB rows of one force component (T(N/2) * RB threads); smem: RB LD float2
+// Called by the 32 threads of warp 0: lane 0 registers the bytes on `bar`, lanes < rb copy one
+// row each (P complex; P is a multiple of 4, so every row is a multiple of 32 bytes).
+__device__ __forceinline__ void c2r3_issue(float2* stage, const float2* src_rows, int rb, int P, int LD,
+                                           uint64_t* bar) {
+  const int lane = threadIdx.x & 31;
+  fence_proxy_async_smem();
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)rb * (uint32_t)P * 8u);
+  __syncwarp();
+  for (int w = lane; w < rb; w += 32) bulk_copy_g2s(stage + w * LD, src_rows + (int64_t)w * P, (uint32_t)P * 8u, bar);
+}
+
+// Inverse x transform of the staged rows into F rows (pitch N floats); comp 0 applies i k_x.
 template <int N, int RB>
-__device__ __forceinline__ void c2r3_body(const float2* __restrict__ C, const float2* __restrict__ Gy,
-                                          const float2* __restrict__ Gz, float* __restrict__ F, int P, float kf,
-                                          const float2* __restrict__ tw, int bx, int comp, float2* smem) {
+__device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ Frows, int comp, float kf,
+                                             const float2* __restrict__ tw) {
   constexpr int M = N / 2, T = FFTConf<M>::T, LD = xrow_ld<M>();
-  const float2* srcm = comp == 0 ? C : (comp == 1 ? Gy : Gz);
+  static_assert(T * RB <= 1024, "block too large");
   const int t = threadIdx.x % T, w = threadIdx.x / T;
-  const int64_t row = (int64_t)bx * RB + w;
-  const float2* src = srcm + row * P;
-  float2* buf = smem + w * LD;
-  for (int k = t; k <= M; k += T) {
-    float2 x = src[k];
-    if (comp == 0) x = mul_ik(x, k == M ? 0.0f : kf * (float)k);
-    buf[xpad(k)] = x;
-  }
-  __syncthreads();
+  float2* buf = stage + w * LD;
+  auto X = [&](int k) -> float2 {
+    const float2 x = buf[k];
+    return comp == 0 ? mul_ik(x, k == M ? 0.0f : kf * (float)k) : x;
+  };
   auto load = [&](int n) -> float2 {
-    const float2 a = buf[xpad(n)], bb = c_conj(buf[xpad(M - n)]);
+    const float2 a = X(n), bb = c_conj(X(M - n));
     const float2 e = c_add(a, bb);
     const float2 o = c_mul(c_sub(a, bb), c_conj(__ldg(tw + n)));
     return make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
   };
   auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
-  float2* dst = reinterpret_cast<float2*>(F + (int64_t)comp * N * N * N + row * N);
+  float2* dst = reinterpret_cast<float2*>(Frows + (int64_t)w * N);
   auto store = [&](int n, float2 x) { dst[n] = x; };
   fft_1d<M, 2, true>(t, tw, load, mem, store);
 }

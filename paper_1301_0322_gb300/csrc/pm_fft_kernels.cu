@@ -42,12 +42,44 @@ __global__ void __launch_bounds__(FFTConf<N>::T * green_width<N>(), 2)
   y_inv3_body<N, green_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
+// Persistent: each block walks items blockIdx.x, blockIdx.x + gridDim.x, ... with the bulk
+// copy of the next item in flight during the transform of the current one (double buffer).
 template <int N>
-__global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 2)
+__global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 3)
     k_fft_x_c2r3(const float2* __restrict__ C, const float2* __restrict__ Gy, const float2* __restrict__ Gz,
-                 float* __restrict__ F, int P, float kf, const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  c2r3_body<N, c2r3_rows<N>()>(C, Gy, Gz, F, P, kf, tw, blockIdx.x, blockIdx.y, smem);
+                 float* __restrict__ F, int P, float kf, const float2* __restrict__ tw, int* __restrict__ err) {
+  constexpr int M = N / 2, RB = c2r3_rows<N>(), LD = xrow_ld<M>();
+  extern __shared__ __align__(128) float2 c2r_stage[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int64_t nrb = (int64_t)N * N / RB, total = 3 * nrb;
+  auto src_of = [&](int64_t item) -> const float2* {
+    const int comp = (int)(item / nrb);
+    const float2* m = comp == 0 ? C : (comp == 1 ? Gy : Gz);
+    return m + (item - comp * nrb) * RB * P;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int64_t item = blockIdx.x;
+  if (item < total && threadIdx.x < 32) c2r3_issue(c2r_stage, src_of(item), RB, P, LD, &bars[0]);
+  for (int it = 0; item < total; ++it, item += gridDim.x) {
+    const int b = it & 1;
+    const int64_t next = item + gridDim.x;
+    if (next < total && threadIdx.x < 32) c2r3_issue(c2r_stage + (b ^ 1) * RB * LD, src_of(next), RB, P, LD, &bars[b ^ 1]);
+    const bool ok = mbar_wait(&bars[b], (it >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+      if (next < total) mbar_wait(&bars[b ^ 1], ((it + 1) >> 1) & 1);
+      return;
+    }
+    const int comp = (int)(item / nrb);
+    const int64_t row0 = (item - comp * nrb) * RB;
+    c2r3_compute<N, RB>(c2r_stage + b * RB * LD, F + (int64_t)comp * N * N * N + row0 * N, comp, kf, tw);
+    __syncthreads();
+  }
 }
 
 // ---- launchers ---------------------------------------------------------------------------------------------------
@@ -117,16 +149,27 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const float* s, co
     k_fft_y_inv3<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gy, Gz, P, kf, tw);
     COLA_LAUNCH_CHECK();
   }
-  // 5. inverse x passes
+  // 5. inverse x passes (persistent, bulk-copy pipelined)
   {
-    constexpr int RB = c2r3_rows<N>();
-    const size_t smem = sizeof(float2) * RB * xrow_ld<M>();
+    constexpr int RB = c2r3_rows<N>(), T = FFTConf<M>::T;
+    const size_t smem = sizeof(float2) * 2 * RB * xrow_ld<M>();
     if ((rc = set_smem(k_fft_x_c2r3<N>, smem))) return rc;
     const int64_t nrows = (int64_t)N * N;
     if (nrows % RB) return fail(COLA_EINVAL, "fused c2r: row count not a multiple of the block rows");
-    dim3 grid((unsigned)(nrows / RB), 3);
+    if (P % 4) return fail(COLA_EINVAL, "fused c2r: row pitch must be a multiple of 4 complex");
+    static int grid_cap = 0;
+    if (!grid_cap) {
+      int occ = 0, dev = 0, sms = 0;
+      COLA_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_x_c2r3<N>, T * RB, smem));
+      COLA_CUDA_CHECK(cudaGetDevice(&dev));
+      COLA_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      if (occ < 1) return fail(COLA_EUNSUPPORTED, "fused c2r does not fit on an SM");
+      grid_cap = occ * sms;
+    }
+    const int64_t items = 3 * nrows / RB;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, grid_cap);
     LaunchScope ls_(flabel<N>(3), st);
-    k_fft_x_c2r3<N><<<grid, FFTConf<M>::T * RB, smem, st>>>(A, Gy, Gz, F, P, kf, tw);
+    k_fft_x_c2r3<N><<<grid, T * RB, smem, st>>>(A, Gy, Gz, F, P, kf, tw, err);
     COLA_LAUNCH_CHECK();
   }
   return COLA_OK;
