@@ -32,7 +32,6 @@ struct BoxDesc {
   int P, deconv, bin_base, c2r_rb;  // c2r_rb: rows per inverse-x work item
   float kf, norm, dscale;
   int c2r_ld;                        // row pitch (complex) of the staged inverse-x rows
-  int cols_t;                        // threads per column of the column passes, FFTConf<ng>::T
   int64_t pbase;            // first particle of the box in the ensemble arrays
   float2* A;                // half spectrum [ng][ng][P]
   float2* Gy;
@@ -151,20 +150,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
   float2* sm = reinterpret_cast<float2*>(ens_smem);
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int next = item + gridDim.x;
-    if (next < total) {  // L2 prefetch of the next item's input strips
-      const int nb = find_box(starts, nbox, next);
-      const BoxDesc& dn = boxes[nb];
-      const int n = dn.g.ng, W = NT / dn.cols_t, nbx = (n / 2 + 1 + W - 1) / W;
-      const int loc = next - __ldg(starts + nb), bx = loc % nbx, slab = loc / nbx;
-      const int64_t P = dn.P, NP = (int64_t)n * P;
-      if (KIND == 1) {
-        prefetch_strip(dn.A + slab * P, NP, n, bx * W, W, n / 2 + 1, NT);
-      } else {
-        prefetch_strip(dn.A + slab * NP, P, n, bx * W, W, n / 2 + 1, NT);
-        if (KIND == 2) prefetch_strip(dn.Gz + slab * NP, P, n, bx * W, W, n / 2 + 1, NT);
-      }
-    }
     const int b = find_box(starts, nbox, item);
     const BoxDesc& d = boxes[b];
     const int local = item - __ldg(starts + b);
@@ -428,7 +413,6 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     const int M = n / 2;
     const size_t dep = sizeof(unsigned long long) * sh.rows * std::max(n, xrow_ld_host(M));
     const size_t cols = sizeof(float2) * n * sh.W;
-    d.cols_t = host_T(n);
     d.c2r_rb = sh.RB;
     d.c2r_ld = xrow_ld_host(M);
     const size_t c2r = sizeof(float2) * 2 * sh.RB * xrow_ld_host(M);  // two stage buffers

@@ -23,21 +23,12 @@ __host__ __device__ constexpr int x_rows() {
 }
 
 // In-place FFT of ncols columns per slab: element (n, col) at data[slab*slab_stride + n*row_stride + col].
-// Persistent: items (column strip bx, slab) = item % nbx, item / nbx; the next item's strip is
-// prefetched into L2 while the current one is transformed.
 template <int N, bool INV>
 __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
-    k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols, int nbx,
-               int64_t total, const float2* __restrict__ tw) {
-  constexpr int W = col_width<N>(), NT = FFTConf<N>::T * W;
+    k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols,
+               const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
-    const int64_t next = item + gridDim.x;
-    if (next < total)
-      prefetch_strip(data + (next / nbx) * slab_stride, row_stride, N, (int)(next % nbx) * W, W, ncols, NT);
-    cols_body<N, W, INV>(data, slab_stride, row_stride, ncols, tw, (int)(item % nbx), (int)(item / nbx), smem);
-    __syncthreads();
-  }
+  cols_body<N, col_width<N>(), INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
 }
 
 // Real rows of length N -> half-spectrum rows (N/2 + 1 entries, stride P), via a complex
@@ -133,42 +124,21 @@ static int x_c2r(const float2* in, float* out, int64_t nrows, int P, const float
   return COLA_OK;
 }
 
-// blocks of a persistent kernel: resident blocks per SM x SMs (cached per kernel)
-template <class K>
-static int persistent_blocks(K kernel, int threads, size_t smem, int& cache) {
-  if (!cache) {
-    int occ = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) return 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cache = occ * sms;
-  }
-  return cache;
-}
-
 template <int N>
 static int cols(bool inverse, float2* data, int64_t nslabs, int64_t slab_stride, int64_t row_stride, int ncols,
                 const float2* tw, cudaStream_t st) {
-  constexpr int W = col_width<N>(), NT = FFTConf<N>::T * W;
+  constexpr int W = col_width<N>();
   const size_t smem = (size_t)N * W * sizeof(float2);
-  if (nslabs > 0x7fffffff) return fail(COLA_EINVAL, "fft column pass: too many slabs");
-  const int nbx = (ncols + W - 1) / W;
-  const int64_t total = nbx * nslabs;
-  static int cap_inv = 0, cap_fwd = 0;
+  if (nslabs > 65535) return fail(COLA_EINVAL, "fft column pass: too many slabs");
+  dim3 grid((ncols + W - 1) / W, (unsigned)nslabs);
   if (inverse) {
     allow_smem(k_fft_cols<N, true>, smem);
-    const int cap = persistent_blocks(k_fft_cols<N, true>, NT, smem, cap_inv);
-    if (cap < 1) return fail(COLA_ECUDA, "fft column pass: occupancy query failed");
     { LaunchScope ls_(label<N>("inv"), st);
-    k_fft_cols<N, true><<<(unsigned)std::min<int64_t>(total, cap), NT, smem, st>>>(data, slab_stride, row_stride,
-                                                                                   ncols, nbx, total, tw); }
+    k_fft_cols<N, true><<<grid, FFTConf<N>::T * W, smem, st>>>(data, slab_stride, row_stride, ncols, tw); }
   } else {
     allow_smem(k_fft_cols<N, false>, smem);
-    const int cap = persistent_blocks(k_fft_cols<N, false>, NT, smem, cap_fwd);
-    if (cap < 1) return fail(COLA_ECUDA, "fft column pass: occupancy query failed");
     { LaunchScope ls_(label<N>("fwd"), st);
-    k_fft_cols<N, false><<<(unsigned)std::min<int64_t>(total, cap), NT, smem, st>>>(data, slab_stride, row_stride,
-                                                                                    ncols, nbx, total, tw); }
+    k_fft_cols<N, false><<<grid, FFTConf<N>::T * W, smem, st>>>(data, slab_stride, row_stride, ncols, tw); }
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;

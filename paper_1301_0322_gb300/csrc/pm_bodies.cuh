@@ -44,20 +44,6 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
   fft_1d<N, 1, INV>(t, tw, load, mem, store);
 }
 
-// L2 prefetch of the strip a column item reads: `rows` rows (row r at base + r * row_stride) of
-// the columns [col0, col0 + W) that exist (< ncols), spread over the block's nt threads.  The
-// persistent column kernels issue it for their next item before transforming the current
-// one, so the strip's DRAM reads overlap the transform.  Rows are padded (pitch >= ncols + 1
-// for odd ncols), so rounding the width up to whole 16-byte units stays inside the row.
-__device__ __forceinline__ void prefetch_strip(const float2* base, int64_t row_stride, int rows, int col0, int W,
-                                               int ncols, int nt) {
-  const int cols = min(W, ncols - col0);
-  if (cols <= 0) return;
-  const uint32_t bytes = (uint32_t)((cols + 1) & ~1) * 8u;
-  const float2* p = base + col0;
-  for (int r = threadIdx.x; r < rows; r += nt) prefetch_l2(p + (int64_t)r * row_stride, bytes);
-}
-
 // ---- 1. deposit + x r2c -----------------------------------------------------------------------
 // block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
 // bytes of shared memory; ints: 28 ints of shared memory

@@ -26,40 +26,20 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ)
   deposit_fftx_body<N, TY, TZ>(g, tl, s, idx, offsets, out, P, tw, dscale, err, blockIdx.x, acc, ints);
 }
 
-// Persistent column passes: items (column strip bx, slab) = item % nbx, item / nbx; the next
-// item's input strips are prefetched into L2 while the current one is transformed.
 template <int N>
 __global__ void __launch_bounds__(FFTConf<N>::T * green_width<N>(), 2)
     k_fft_z_green(float2* __restrict__ A, float2* __restrict__ Gz, int P, float kf, int deconv, float norm,
                   const float2* __restrict__ tw) {
-  constexpr int W = green_width<N>(), NT = FFTConf<N>::T * W, nh = N / 2 + 1, nbx = (nh + W - 1) / W;
-  constexpr int total = nbx * N;
   extern __shared__ float2 sm[];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int next = item + gridDim.x;
-    if (next < total) prefetch_strip(A + (int64_t)(next / nbx) * P, (int64_t)N * P, N, (next % nbx) * W, W, nh, NT);
-    z_green_body<N, W>(A, Gz, P, kf, deconv, norm, tw, item % nbx, item / nbx, sm);
-    __syncthreads();
-  }
+  z_green_body<N, green_width<N>()>(A, Gz, P, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int N>
 __global__ void __launch_bounds__(FFTConf<N>::T * green_width<N>(), 2)
     k_fft_y_inv3(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz, int P, float kf,
                  const float2* __restrict__ tw) {
-  constexpr int W = green_width<N>(), NT = FFTConf<N>::T * W, nh = N / 2 + 1, nbx = (nh + W - 1) / W;
-  constexpr int total = nbx * N;
   extern __shared__ float2 sm[];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int next = item + gridDim.x;
-    if (next < total) {
-      const int64_t slab = (int64_t)(next / nbx) * N * P;
-      prefetch_strip(B + slab, P, N, (next % nbx) * W, W, nh, NT);
-      prefetch_strip(Gz + slab, P, N, (next % nbx) * W, W, nh, NT);
-    }
-    y_inv3_body<N, W>(B, Gy, Gz, P, kf, tw, item % nbx, item / nbx, sm);
-    __syncthreads();
-  }
+  y_inv3_body<N, green_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
 // Persistent: each block walks items blockIdx.x, blockIdx.x + gridDim.x, ... with the bulk
@@ -111,20 +91,6 @@ static int set_smem(K kernel, size_t bytes) {
   return COLA_OK;
 }
 
-// blocks of a persistent launch: resident blocks per SM x SMs, queried once per kernel
-template <class K>
-static int grid_cap(K kernel, int threads, size_t smem, int& cache) {
-  if (!cache) {
-    int occ = 0, dev = 0, sms = 0;
-    COLA_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem));
-    COLA_CUDA_CHECK(cudaGetDevice(&dev));
-    COLA_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (occ < 1) return fail(COLA_EUNSUPPORTED, "persistent kernel does not fit on an SM");
-    cache = occ * sms;
-  }
-  return COLA_OK;
-}
-
 template <int N>
 static const char* flabel(int kind) {
   static const std::string names[4] = {std::string("deposit_fftx_") + std::to_string(N),
@@ -169,22 +135,18 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const float* s, co
   {
     const size_t smem = sizeof(float2) * 2 * N * W;
     if ((rc = set_smem(k_fft_z_green<N>, smem))) return rc;
-    static int cap = 0;
-    if ((rc = grid_cap(k_fft_z_green<N>, FFTConf<N>::T * W, smem, cap))) return rc;
-    const int items = (nh + W - 1) / W * N;
+    dim3 grid((nh + W - 1) / W, N);
     LaunchScope ls_(flabel<N>(1), st);
-    k_fft_z_green<N><<<std::min(items, cap), FFTConf<N>::T * W, smem, st>>>(A, Gz, P, kf, deconv, norm, tw);
+    k_fft_z_green<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gz, P, kf, deconv, norm, tw);
     COLA_LAUNCH_CHECK();
   }
   // 4. inverse y passes
   {
     const size_t smem = sizeof(float2) * 2 * N * W;
     if ((rc = set_smem(k_fft_y_inv3<N>, smem))) return rc;
-    static int cap = 0;
-    if ((rc = grid_cap(k_fft_y_inv3<N>, FFTConf<N>::T * W, smem, cap))) return rc;
-    const int items = (nh + W - 1) / W * N;
+    dim3 grid((nh + W - 1) / W, N);
     LaunchScope ls_(flabel<N>(2), st);
-    k_fft_y_inv3<N><<<std::min(items, cap), FFTConf<N>::T * W, smem, st>>>(A, Gy, Gz, P, kf, tw);
+    k_fft_y_inv3<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gy, Gz, P, kf, tw);
     COLA_LAUNCH_CHECK();
   }
   // 5. inverse x passes (persistent, bulk-copy pipelined)
@@ -195,10 +157,17 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const float* s, co
     const int64_t nrows = (int64_t)N * N;
     if (nrows % RB) return fail(COLA_EINVAL, "fused c2r: row count not a multiple of the block rows");
     if (P % 4) return fail(COLA_EINVAL, "fused c2r: row pitch must be a multiple of 4 complex");
-    static int cap = 0;
-    if ((rc = grid_cap(k_fft_x_c2r3<N>, T * RB, smem, cap))) return rc;
+    static int grid_cap = 0;
+    if (!grid_cap) {
+      int occ = 0, dev = 0, sms = 0;
+      COLA_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_x_c2r3<N>, T * RB, smem));
+      COLA_CUDA_CHECK(cudaGetDevice(&dev));
+      COLA_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      if (occ < 1) return fail(COLA_EUNSUPPORTED, "fused c2r does not fit on an SM");
+      grid_cap = occ * sms;
+    }
     const int64_t items = 3 * nrows / RB;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, cap);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, grid_cap);
     LaunchScope ls_(flabel<N>(3), st);
     k_fft_x_c2r3<N><<<grid, T * RB, smem, st>>>(A, Gy, Gz, F, P, kf, tw, err);
     COLA_LAUNCH_CHECK();
