@@ -167,7 +167,7 @@ def loss_and_gradient(noise, target, cfg):
     fw = forward_with_checkpoints(noise, cfg)
     delta = final_density(fw["s"], cfg)
     loss = float(np.sum((delta - target) ** 2))
-    a, mid = time_grid(cfg.a_init, cfg.a_final, cfg.nsteps)
+    a, mid = time_grid(cfg.a_init, cfg.a_final, cfg.nsteps, cfg.spacing)
     g = cosmo.growth(a)
     q = mesh.lattice_q(cfg.n_p, cfg.box)
     npart = cfg.n_p**3

@@ -14,6 +14,9 @@ Paper passages (arXiv:1301.0322, App. A):
     int (a/a_c)/Q da; the leading minus sign printed in its Kick is read as a plus (with it,
     setting s1 = s2 = 0 would not give back eq. KDKStd, as the paper says it does);
   * eq. KDKStd (scheme "pm_std"): the standard leapfrog, no LPT frame, no L+-.
+  * scheme "cola_u1": eq. KDKALC with u = 1 in the Drift and u = a^nLPT in the Kick (the
+    variant of the footnote on the ansatz u = A + B a^nLPT, App. A.3.2).
+  * time grid (cfg.spacing): uniform in a ("a", App. A.3.2) or in ln a ("loga", App. A.2).
   * 2LPT initial conditions: x = q + D1(a0) s1 + D2(a0) s2, v = T[D1](a0) s1 + T[D2](a0) s2.
 
 State: the displacement s with x = q + s (eq. eom), positions taken modulo L for the mesh.
@@ -38,6 +41,7 @@ class ColaConfig:
     a_init: float = 0.1
     a_final: float = 1.0
     deconv: int = 1
+    spacing: str = "a"
 
 
 def acceleration(s, cfg, a):
@@ -61,10 +65,12 @@ def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=Non
     if accel_fn is None:
         accel_fn = lambda s_, a_: acceleration(s_, cfg, a_)
     cosmo = cfg.cosmo
-    a, mid = time_grid(cfg.a_init, cfg.a_final, cfg.nsteps)
+    a, mid = time_grid(cfg.a_init, cfg.a_final, cfg.nsteps, cfg.spacing)
     g = cosmo.growth(a)
     D1, D2, TD1, TD2, T2D1, T2D2 = (g[k] for k in ("D1", "D2", "TD1", "TD2", "T2D1", "T2D2"))
-    lpt = scheme in ("cola", "cola_std")
+    if scheme not in ("cola", "cola_std", "pm_std", "cola_u1"):
+        raise ValueError(f"unknown scheme {scheme!r}")
+    lpt = scheme in ("cola", "cola_std", "cola_u1")
     if not lpt:
         zero = np.zeros_like(s1)
         s1_frame, s2_frame = zero, zero
@@ -79,7 +85,7 @@ def evolve(s1, s2, cfg, scheme="cola", stop_after=None, offset=0.0, accel_fn=Non
 
     def kick(v, ai, af, ic, accel):
         ac = a[ic]
-        if scheme == "cola":
+        if scheme in ("cola", "cola_u1"):
             coef = cosmo.kick_cola(ai, af, ac, cfg.n_lpt)
         elif scheme == "cola_std":
             coef = cosmo.kick_std(ai, af, ac)

@@ -216,8 +216,18 @@ class Cosmology:
         return self.amplitude * k**self.n_s * self.transfer_bbks(k) ** 2
 
 
-def time_grid(a_init, a_final, nsteps):
-    """Scale factors a_0..a_n uniform in a (App. A.3.2) and midpoints a_{i+1/2} (App. A.2)."""
-    a = a_init + (a_final - a_init) * np.arange(nsteps + 1, dtype=np.float64) / nsteps
-    a[-1] = a_final
+def time_grid(a_init, a_final, nsteps, spacing="a"):
+    """Scale factors a_0..a_n and midpoints a_{i+1/2} = (a_i + a_{i+1}) / 2 (App. A.2).
+
+    spacing "a": uniform in a, the grid of the optimal COLA variant (App. A.3.2);
+    spacing "loga": uniform in ln a, the grid App. A.2 finds better for the standard leapfrog.
+    The midpoint rule is the one App. A.2 states for small steps; it is kept for both grids."""
+    i = np.arange(nsteps + 1, dtype=np.float64) / nsteps
+    if spacing == "a":
+        a = a_init + (a_final - a_init) * i
+    elif spacing == "loga":
+        a = a_init * (a_final / a_init) ** i
+    else:
+        raise ValueError(f"unknown spacing {spacing!r}")
+    a[0], a[-1] = a_init, a_final
     return a, 0.5 * (a[:-1] + a[1:])

@@ -157,3 +157,12 @@ def test_time_grid_uniform_in_a():
     assert a[0] == 0.1 and a[-1] == 1.0 and len(a) == 11
     assert np.allclose(np.diff(a), 0.09, rtol=1e-12)
     assert np.allclose(mid, a[:-1] + 0.045, rtol=1e-12)
+
+
+def test_time_grid_uniform_in_log_a():
+    a, mid = time_grid(0.02, 1.0, 8, "loga")
+    assert a[0] == 0.02 and a[-1] == 1.0 and len(a) == 9
+    assert np.allclose(a[1:] / a[:-1], 50.0 ** (1.0 / 8.0), rtol=1e-12)
+    assert np.allclose(mid, 0.5 * (a[:-1] + a[1:]), rtol=1e-15)
+    with pytest.raises(ValueError):
+        time_grid(0.1, 1.0, 4, "linear")

@@ -76,7 +76,7 @@ def test_2lpt_solves_lagrangian_eom_to_second_order(a):
 
 
 @pytest.mark.parametrize("nsteps", [1, 3, 10])
-@pytest.mark.parametrize("scheme", ["cola", "cola_std"])
+@pytest.mark.parametrize("scheme", ["cola", "cola_std", "cola_u1"])
 def test_cola_operators_exact_with_2lpt_force(nsteps, scheme):
     cosmo = Cosmology()
     n, box = 8, 100.0
@@ -124,3 +124,42 @@ def test_full_run_conserves_momentum():
         assert np.abs(out[key].sum(axis=1)).max() < 1e-9 * np.abs(out[key]).sum()
     v = out["v"]
     assert np.abs(v.sum(axis=1)).max() < 1e-9 * np.abs(v).sum()
+
+
+@pytest.mark.parametrize("scheme", ["cola", "cola_std", "cola_u1", "pm_std"])
+@pytest.mark.parametrize("spacing", ["a", "loga"])
+def test_scheme_coefficients_match_eds_closed_forms(scheme, spacing):
+    # Einstein-de Sitter (Q = a^(3/2)), no LPT frame (s1 = s2 = 0) and a uniform acceleration c:
+    # the run reduces to v += c_K c, s += c_D v with the closed forms
+    #   eq. KDKALC:    c_K = (af^n - ai^n) / (n ac^(n+1/2)),  c_D = (af^(n-1/2) - ai^(n-1/2)) / ((n-1/2) ac^n)
+    #   eq. KDKALCstd / KDKStd: c_K = 2 (af^(1/2) - ai^(1/2)) / ac,  c_D = 2 (ai^(-1/2) - af^(-1/2))
+    # and "cola_u1" = the KDKALC Kick with the standard Drift (u = 1 in the Drift).
+    n, nsteps, a0, a1 = -2.5, 4, 0.1, 1.0
+    cfg = ColaConfig(n_p=2, n_g=4, box=10.0, cosmo=Cosmology(omega_m=1.0, omega_l=0.0), n_lpt=n, nsteps=nsteps,
+                     a_init=a0, a_final=a1, spacing=spacing)
+    zero = np.zeros((3, 8))
+    c = np.array([1.0, -2.0, 0.5])[:, None] * np.ones((3, 8))
+    out = evolve(zero, zero, cfg, scheme=scheme, accel_fn=lambda s_, a_: c)
+    if spacing == "a":
+        a = a0 + (a1 - a0) * np.arange(nsteps + 1) / nsteps
+    else:
+        a = a0 * (a1 / a0) ** (np.arange(nsteps + 1) / nsteps)
+    mid = 0.5 * (a[:-1] + a[1:])
+
+    def kick(ai, af, ac):
+        if scheme in ("cola", "cola_u1"):
+            return (af**n - ai**n) / (n * ac ** (n + 0.5))
+        return 2.0 * (af**0.5 - ai**0.5) / ac
+
+    def drift(ai, af, ac):
+        if scheme == "cola":
+            return (af ** (n - 0.5) - ai ** (n - 0.5)) / ((n - 0.5) * ac**n)
+        return 2.0 * (ai**-0.5 - af**-0.5)
+
+    s_ref, v_ref = np.zeros(3), np.zeros(3)
+    for i in range(nsteps):
+        v_ref = v_ref + kick(a[i], mid[i], a[i]) * c[:, 0]
+        s_ref = s_ref + drift(a[i], a[i + 1], mid[i]) * v_ref
+        v_ref = v_ref + kick(mid[i], a[i + 1], a[i + 1]) * c[:, 0]
+    assert np.allclose(out["s"][:, 0], s_ref, rtol=1e-9, atol=0)
+    assert np.allclose(out["v"][:, 0], v_ref, rtol=1e-9, atol=0)
