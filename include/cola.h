@@ -72,10 +72,27 @@ typedef struct {
   int32_t deconv;     /* CIC deconvolution power p in 1/W(k)^p of the force: 0, 1 (default), 2 */
   int32_t fixed_bits; /* F: CIC positions are quantised to 2^-F cell (default 16, 8..20)      */
   int32_t adjoint;    /* 1: also reserve the workspace of cola_step_adjoint (3 more meshes)      */
+  int32_t scheme;     /* Kick/Drift operators, one of COLA_SCHEME_* below (default COLA)         */
+  int32_t log_a;      /* 0: steps uniform in a (default, App. A.3.2); 1: uniform in ln a (App. A.2) */
 } cola_config;
 
+/* Time integrators (cola_config.scheme).  All use the merged Kicks of eq. ALCtimestep.
+ *  COLA_SCHEME_COLA     eq. KDKALC, u = a^nLPT in Kick and Drift (the paper's optimal variant)
+ *  COLA_SCHEME_COLA_STD eq. KDKALCstd: the LPT frame with the standard coefficients
+ *                       int (a/a_c)/Q da (Kick) and int da/Q (Drift)
+ *  COLA_SCHEME_PM       eq. KDKStd: standard PM leapfrog, no LPT frame (s1, s2 only set the
+ *                       2LPT initial conditions; v starts at T[D1] s1 + T[D2] s2, no L+-)
+ *  COLA_SCHEME_COLA_U1  eq. KDKALC with u = 1 in the Drift, u = a^nLPT in the Kick (the
+ *                       footnote on u = A + B a^nLPT, App. A.3.2)
+ * The mid-point scale factor is a_{i+1/2} = (a_i + a_{i+1}) / 2 on either grid (App. A.2). */
+#define COLA_SCHEME_COLA 0
+#define COLA_SCHEME_COLA_STD 1
+#define COLA_SCHEME_PM 2
+#define COLA_SCHEME_COLA_U1 3
+
 /* Fill *cfg with the 32^3-particle / 64^3-mesh defaults (L = 100 Mpc/h, Om = 0.27, OL = 0.73,
- * h = 0.7, sigma8 = 0.8, ns = 0.96, nLPT = -2.5, 10 steps from a = 0.1 to 1, deconv 1, F 16). */
+ * h = 0.7, sigma8 = 0.8, ns = 0.96, nLPT = -2.5, 10 steps uniform in a from a = 0.1 to 1,
+ * deconv 1, F 16, scheme COLA). */
 int cola_config_default(cola_config* cfg);
 
 /* Validate cfg and build a plan: float64 growth factors and step coefficients on the host

@@ -37,7 +37,12 @@ class cola_config(ctypes.Structure):
     _fields_ = [("np", ctypes.c_int64), ("ng", ctypes.c_int64), ("box", ctypes.c_double),
                 ("cosmo", cola_cosmo), ("n_lpt", ctypes.c_double), ("nsteps", ctypes.c_int32),
                 ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("deconv", ctypes.c_int32),
-                ("fixed_bits", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
+                ("fixed_bits", ctypes.c_int32), ("adjoint", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("log_a", ctypes.c_int32)]
+
+
+# cola_config.scheme values (include/cola.h) and the oracle's names for them
+SCHEMES = {"cola": 0, "cola_std": 1, "pm_std": 2, "cola_u1": 3}
 
 
 class cola_ensemble_tuning(ctypes.Structure):
@@ -299,12 +304,9 @@ class Plan:
 
     def __init__(self, np_side=32, ng=64, box=100.0, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96,
                  n_lpt=-2.5, nsteps=10, a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, adjoint=False,
-                 device="cuda"):
-        cfg = cola_config_default()
-        cfg.np, cfg.ng, cfg.box = int(np_side), int(ng), float(box)
-        cfg.cosmo = cola_cosmo(omega_m, omega_l, h, sigma8, n_s)
-        cfg.n_lpt, cfg.nsteps, cfg.a_init, cfg.a_final = float(n_lpt), int(nsteps), float(a_init), float(a_final)
-        cfg.deconv, cfg.fixed_bits, cfg.adjoint = int(deconv), int(fixed_bits), int(bool(adjoint))
+                 scheme="cola", log_a=False, device="cuda"):
+        cfg = _make_config(np_side, ng, box, omega_m, omega_l, h, sigma8, n_s, n_lpt, nsteps, a_init, a_final, deconv,
+                           fixed_bits, adjoint, scheme, log_a)
         self.cfg = cfg
         self.np, self.ng, self.nsteps = int(np_side), int(ng), int(nsteps)
         self.n3 = self.np**3
@@ -401,12 +403,14 @@ class Plan:
 
 
 def _make_config(np_side, ng, box, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8, n_s=0.96, n_lpt=-2.5, nsteps=10,
-                 a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, adjoint=False):
+                 a_init=0.1, a_final=1.0, deconv=1, fixed_bits=16, adjoint=False, scheme="cola", log_a=False):
     cfg = cola_config_default()
     cfg.np, cfg.ng, cfg.box = int(np_side), int(ng), float(box)
     cfg.cosmo = cola_cosmo(omega_m, omega_l, h, sigma8, n_s)
     cfg.n_lpt, cfg.nsteps, cfg.a_init, cfg.a_final = float(n_lpt), int(nsteps), float(a_init), float(a_final)
     cfg.deconv, cfg.fixed_bits, cfg.adjoint = int(deconv), int(fixed_bits), int(bool(adjoint))
+    cfg.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    cfg.log_a = int(bool(log_a))
     return cfg
 
 

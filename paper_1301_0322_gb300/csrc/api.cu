@@ -145,6 +145,8 @@ int cola_config_default(cola_config* cfg) {
   cfg->deconv = 1;
   cfg->fixed_bits = 16;
   cfg->adjoint = 0;
+  cfg->scheme = COLA_SCHEME_COLA;
+  cfg->log_a = 0;
   return COLA_OK;
 }
 
@@ -162,6 +164,10 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   if (c.deconv < 0 || c.deconv > 2) return fail(COLA_EINVAL, "deconv must be 0, 1 or 2");
   if (c.fixed_bits < 8 || c.fixed_bits > 20) return fail(COLA_EINVAL, "fixed_bits must be in [8, 20]");
   if (c.adjoint != 0 && c.adjoint != 1) return fail(COLA_EINVAL, "adjoint must be 0 or 1");
+  if (c.scheme < COLA_SCHEME_COLA || c.scheme > COLA_SCHEME_COLA_U1) return fail(COLA_EINVAL, "unknown scheme");
+  if (c.log_a != 0 && c.log_a != 1) return fail(COLA_EINVAL, "log_a must be 0 or 1");
+  if (c.adjoint && c.scheme == COLA_SCHEME_PM)
+    return fail(COLA_EINVAL, "the adjoint calls assume the LPT frame (v = 0 after L-): not with COLA_SCHEME_PM");
   if (!(c.cosmo.omega_m > 0) || !(c.cosmo.h > 0) || !(c.cosmo.sigma8 > 0))
     return fail(COLA_EINVAL, "omega_m, h and sigma8 must be positive");
   cola_plan* p = new cola_plan();
@@ -191,14 +197,16 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   for (int i = 0; i <= c.nsteps; ++i) {
     const double* r = &p->coef64[(size_t)i * COLA_NCOEF];
     float* o = &p->coef32[(size_t)i * kCoef32];
+    // the standard leapfrog has no LPT frame: no -T^2[D] s terms, no dD s drift, no L+
+    const double frame = c.scheme == COLA_SCHEME_PM ? 0.0 : 1.0;
     o[kCKF] = (float)(r[2] * r[1]);
-    o[kCK1] = (float)(r[2] * r[3]);
-    o[kCK2] = (float)(r[2] * r[4]);
+    o[kCK1] = (float)(frame * r[2] * r[3]);
+    o[kCK2] = (float)(frame * r[2] * r[4]);
     o[kCD] = (float)r[5];
-    o[kDD1] = (float)r[6];
-    o[kDD2] = (float)r[7];
-    o[kTD1] = (float)r[8];
-    o[kTD2] = (float)r[9];
+    o[kDD1] = (float)(frame * r[6]);
+    o[kDD2] = (float)(frame * r[7]);
+    o[kTD1] = (float)(frame * r[8]);
+    o[kTD2] = (float)(frame * r[9]);
     o[kLast] = i == c.nsteps ? 1.0f : 0.0f;
   }
   twiddle_table((int)c.ng, p->tw_g);
@@ -290,8 +298,12 @@ int cola_ic_2lpt(cola_plan* plan, const float* noise, float* s, float* v, float*
     if ((rc = launch_kmul(n, P, box, 0, j, 0, s2scale, w.icC1, w.icC0, st))) return rc;
     if ((rc = fft3d_c2r(n, P, w.icC0, s2 + j * n3, w.tw_p, 1.0f, st))) return rc;
   }
+  // v = T[s] after L- (eq. Lops): 0 in the LPT frame; the standard leapfrog starts from the
+  // full 2LPT velocity T[D1] s1 + T[D2] s2
   const double* row0 = plan->coef64.data();
-  return launch_ic_assemble(n3, (float)row0[10], (float)row0[11], s1, s2, s, v, st);
+  const bool pm = plan->cfg.scheme == COLA_SCHEME_PM;
+  return launch_ic_assemble(n3, (float)row0[10], (float)row0[11], pm ? (float)row0[8] : 0.0f,
+                            pm ? (float)row0[9] : 0.0f, s1, s2, s, v, st);
 }
 
 int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1, const float* s2,

@@ -7,6 +7,7 @@
 //  D1(1) = 1, D2 = D2u / D2u(1)                                                     (App. A.3)
 //  Kick:  c_K = (u(kb) - u(ka)) / T[u](a_c),  Drift: c_D = int_{ai}^{af} u/Q da / u(a_c),
 //  u = a^nLPT                                                                      (eq. KDKALC)
+//  standard coefficients: c_K = int (a/a_c)/Q da, c_D = int da/Q           (eqs. KDKStd, KDKALCstd)
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -116,7 +117,10 @@ int build_coefficients(const cola_config& cfg, std::vector<double>& table, doubl
   const Background bg{cfg.cosmo.omega_m, cfg.cosmo.omega_l, 1.0 - cfg.cosmo.omega_m - cfg.cosmo.omega_l};
   const int n = cfg.nsteps;
   std::vector<double> a(n + 1), mid(n);
-  for (int i = 0; i <= n; ++i) a[i] = cfg.a_init + (cfg.a_final - cfg.a_init) * i / n;
+  for (int i = 0; i <= n; ++i)
+    a[i] = cfg.log_a ? cfg.a_init * std::pow(cfg.a_final / cfg.a_init, (double)i / n)
+                     : cfg.a_init + (cfg.a_final - cfg.a_init) * i / n;
+  a[0] = cfg.a_init;
   a[n] = cfg.a_final;
   for (int i = 0; i < n; ++i) mid[i] = 0.5 * (a[i] + a[i + 1]);
 
@@ -138,7 +142,10 @@ int build_coefficients(const cola_config& cfg, std::vector<double>& table, doubl
   const double nl = cfg.n_lpt;
   auto u = [&](double x) { return std::pow(x, nl); };
   auto Tu = [&](double x) { return bg.Q(x) * nl * std::pow(x, nl - 1.0); };
+  const bool modified_kick = cfg.scheme == COLA_SCHEME_COLA || cfg.scheme == COLA_SCHEME_COLA_U1;
+  const bool modified_drift = cfg.scheme == COLA_SCHEME_COLA;
   auto kick = [&](double ka, double kb, double ac) {
+    if (!modified_kick) return drift_integral(bg, ka, kb, 1.0) / ac;  // int (a/a_c)/Q da
     if (std::fabs(nl) < 1e-12) return std::log(kb / ka) * ac / bg.Q(ac);
     return (u(kb) - u(ka)) / Tu(ac);
   };
@@ -159,7 +166,8 @@ int build_coefficients(const cola_config& cfg, std::vector<double>& table, doubl
     row[4] = 1.5 * om * a[i] * (D2un - D1 * D1) / d2u1;
     if (i < n) {
       const GrowthState& h = at(a[i + 1]);
-      row[5] = drift_integral(bg, a[i], a[i + 1], nl) / u(mid[i]);
+      row[5] = modified_drift ? drift_integral(bg, a[i], a[i + 1], nl) / u(mid[i])
+                              : drift_integral(bg, a[i], a[i + 1], 0.0);  // int da/Q
       row[6] = h.d1 / g1.d1 - D1;
       row[7] = h.d2 / (g1.d1 * g1.d1) / d2u1 - D2un / d2u1;
       row[14] = a[i + 1];

@@ -144,8 +144,8 @@ int launch_kmul(int n, int P, double box, int kind, int i, int j, float scale, c
 int launch_source_2lpt(int64_t n3, const float* fxx, const float* fyy, const float* fzz, float* out_acc,
                        cudaStream_t st);
 int launch_source_sub_sq(int64_t n3, const float* f, float* acc, cudaStream_t st);
-int launch_ic_assemble(int64_t n3, float d1, float d2, const float* s1, const float* s2, float* s, float* v,
-                       cudaStream_t st);
+int launch_ic_assemble(int64_t n3, float d1, float d2, float t1, float t2, const float* s1, const float* s2,
+                       float* s, float* v, cudaStream_t st);
 
 // adjoint kernels (adjoint_kernels.cu)
 int launch_adjoint_pre(int64_t n3, int mode, const float* coef, float* lam_s, float* lam_v, float* lam_s1,

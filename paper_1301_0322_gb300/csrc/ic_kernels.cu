@@ -139,11 +139,12 @@ __global__ void k_source_sub_sq(int64_t n3, const float* __restrict__ f, float* 
 }
 
 // s = D1 s1 + D2 s2, v = 0 (2LPT position at a_init; velocity after L-).
-__global__ void k_ic_assemble(int64_t m, float d1, float d2, const float* __restrict__ s1,
+__global__ void k_ic_assemble(int64_t m, float d1, float d2, float t1, float t2, const float* __restrict__ s1,
                               const float* __restrict__ s2, float* __restrict__ s, float* __restrict__ v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    s[i] = fmaf(d1, s1[i], d2 * s2[i]);
-    v[i] = 0.0f;
+    const float a = s1[i], b = s2[i];
+    s[i] = fmaf(d1, a, d2 * b);
+    v[i] = fmaf(t1, a, t2 * b);
   }
 }
 
@@ -201,10 +202,10 @@ int launch_source_sub_sq(int64_t n3, const float* f, float* acc, cudaStream_t st
   return COLA_OK;
 }
 
-int launch_ic_assemble(int64_t n3, float d1, float d2, const float* s1, const float* s2, float* s, float* v,
-                       cudaStream_t st) {
+int launch_ic_assemble(int64_t n3, float d1, float d2, float t1, float t2, const float* s1, const float* s2,
+                       float* s, float* v, cudaStream_t st) {
   { LaunchScope ls_("ic_assemble", st);
-  k_ic_assemble<<<grid_for(3 * n3), 256, 0, st>>>(3 * n3, d1, d2, s1, s2, s, v); }
+  k_ic_assemble<<<grid_for(3 * n3), 256, 0, st>>>(3 * n3, d1, d2, t1, t2, s1, s2, s, v); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }

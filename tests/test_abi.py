@@ -44,13 +44,23 @@ def test_config_validation(lib):
     cfg = lib.cola_config_default()
     assert (cfg.np, cfg.ng, cfg.nsteps, cfg.deconv, cfg.fixed_bits) == (32, 64, 10, 1, 16)
     assert cfg.n_lpt == -2.5 and cfg.a_init == 0.1
+    assert (cfg.scheme, cfg.log_a) == (0, 0)
     for field, bad, code in (("ng", 100, 4), ("np", 7, 4), ("nsteps", 0, 1), ("deconv", 3, 1),
-                             ("fixed_bits", 30, 1), ("a_init", 2.0, 1), ("box", -1.0, 1)):
+                             ("fixed_bits", 30, 1), ("a_init", 2.0, 1), ("box", -1.0, 1), ("scheme", 4, 1),
+                             ("log_a", 2, 1)):
         c = lib.cola_config_default()
         setattr(c, field, bad)
         with pytest.raises(lib.ColaError) as e:
             lib.cola_plan_create(c)
         assert e.value.code == code, field
+
+
+def test_adjoint_needs_the_lpt_frame(lib):
+    c = lib.cola_config_default()
+    c.scheme, c.adjoint = lib.SCHEMES["pm_std"], 1
+    with pytest.raises(lib.ColaError) as e:
+        lib.cola_plan_create(c)
+    assert e.value.code == 1
 
 
 def test_calls_without_workspace_are_rejected(lib):
@@ -65,17 +75,31 @@ def test_calls_without_workspace_are_rejected(lib):
         lib.cola_plan_destroy(h)
 
 
-@pytest.mark.parametrize("om,ol,n_lpt,nsteps", [(0.27, 0.73, -2.5, 10), (1.0, 0.0, -2.5, 3), (0.3, 0.6, 1.5, 5)])
-def test_host_coefficients_match_oracle(lib, om, ol, n_lpt, nsteps):
+@pytest.mark.parametrize("om,ol,n_lpt,nsteps,scheme,log_a", [(0.27, 0.73, -2.5, 10, "cola", 0),
+                                                            (1.0, 0.0, -2.5, 3, "cola", 0),
+                                                            (0.3, 0.6, 1.5, 5, "cola", 0),
+                                                            (0.27, 0.73, -2.5, 10, "cola_std", 0),
+                                                            (0.27, 0.73, -2.5, 10, "pm_std", 1),
+                                                            (0.27, 0.73, -2.0, 6, "cola_u1", 1),
+                                                            (0.27, 0.73, -2.5, 7, "cola", 1)])
+def test_host_coefficients_match_oracle(lib, om, ol, n_lpt, nsteps, scheme, log_a):
     cfg = lib.cola_config_default()
     cfg.cosmo.omega_m, cfg.cosmo.omega_l, cfg.n_lpt, cfg.nsteps = om, ol, n_lpt, nsteps
+    cfg.scheme, cfg.log_a = lib.SCHEMES[scheme], log_a
     h = lib.cola_plan_create(cfg)
     try:
         tab = lib.cola_coeffs(h, nsteps)
     finally:
         lib.cola_plan_destroy(h)
     cosmo = Cosmology(omega_m=om, omega_l=ol)
-    a, mid = time_grid(0.1, 1.0, nsteps)
+    a, mid = time_grid(0.1, 1.0, nsteps, "loga" if log_a else "a")
+    modified_kick = scheme in ("cola", "cola_u1")
+
+    def kick(ai, af, ac):
+        return cosmo.kick_cola(ai, af, ac, n_lpt) if modified_kick else cosmo.kick_std(ai, af, ac)
+
+    def drift(ai, af, ac):
+        return cosmo.drift_cola(ai, af, ac, n_lpt) if scheme == "cola" else cosmo.drift_std(ai, af)
     g = cosmo.growth(a)
     for i in range(nsteps + 1):
         ka = a[0] if i == 0 else mid[i - 1]
@@ -84,7 +108,7 @@ def test_host_coefficients_match_oracle(lib, om, ol, n_lpt, nsteps):
         assert row[0] == pytest.approx(a[i], rel=1e-15)
         assert row[1] == pytest.approx(1.5 * om * a[i], rel=1e-14)
         # the merged kick K(a_i-1/2, a_i; a_i) K(a_i, a_i+1/2; a_i) of eq. ALCtimestep
-        merged = cosmo.kick_cola(ka, a[i], a[i], n_lpt) + cosmo.kick_cola(a[i], kb, a[i], n_lpt)
+        merged = kick(ka, a[i], a[i]) + kick(a[i], kb, a[i])
         assert row[2] == pytest.approx(merged, rel=1e-10)
         assert row[3] == pytest.approx(g["T2D1"][i], rel=1e-9)
         assert row[4] == pytest.approx(g["T2D2"][i], rel=1e-8)
@@ -93,7 +117,7 @@ def test_host_coefficients_match_oracle(lib, om, ol, n_lpt, nsteps):
         assert row[10] == pytest.approx(g["D1"][i], rel=1e-9)
         assert row[11] == pytest.approx(g["D2"][i], rel=1e-8)
         if i < nsteps:
-            assert row[5] == pytest.approx(cosmo.drift_cola(a[i], a[i + 1], mid[i], n_lpt), rel=1e-10)
+            assert row[5] == pytest.approx(drift(a[i], a[i + 1], mid[i]), rel=1e-10)
             assert row[6] == pytest.approx(g["D1"][i + 1] - g["D1"][i], rel=1e-8)
             assert row[7] == pytest.approx(g["D2"][i + 1] - g["D2"][i], rel=1e-7)
         assert row[15] == pytest.approx(g["d2u1"], rel=1e-9)

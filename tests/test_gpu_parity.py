@@ -154,14 +154,19 @@ def gpu_run(cola, plan, w):
     return s, v
 
 
-def test_full_run_parity_32p_64g(cola):
+# the paper's optimal variant (eq. KDKALC, steps uniform in a), the other discretisations of
+# App. A (eq. KDKALCstd; the standard PM leapfrog eq. KDKStd; u = 1 in the Drift) and steps
+# uniform in ln a (App. A.2)
+@pytest.mark.parametrize("scheme,log_a", [("cola", False), ("cola_std", False), ("pm_std", False),
+                                          ("cola_u1", False), ("cola", True), ("pm_std", True)])
+def test_full_run_parity_32p_64g(cola, scheme, log_a):
     n_p, ng, box = 32, 64, 100.0
-    plan = cola.Plan(np_side=n_p, ng=ng, box=box)
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, scheme=scheme, log_a=log_a)
     w = inputs.gaussian_noise(n_p, 1)
     s, v = gpu_run(cola, plan, w)
     sg, vg = host(s), host(v)
-    cfg = ocola.ColaConfig(n_p=n_p, n_g=ng, box=box)
-    ref = ocola.run(w.reshape(n_p, n_p, n_p).astype(np.float64), cfg)
+    cfg = ocola.ColaConfig(n_p=n_p, n_g=ng, box=box, spacing="loga" if log_a else "a")
+    ref = ocola.run(w.reshape(n_p, n_p, n_p).astype(np.float64), cfg, scheme=scheme)
     cell = box / ng
     ds = np.abs(sg - ref["s"]).max() / cell
     print("max |ds| in cells:", ds, " max |dv|/rms v:", np.abs(vg - ref["v"]).max() / np.sqrt(np.mean(ref["v"] ** 2)))
