@@ -49,3 +49,45 @@ def power_spectrum(delta, box, nbins, deconvolve=True):
         kmean = np.where(nmodes > 0, ksum / nmodes, 0.0)
         pmean = np.where(nmodes > 0, psum / nmodes, 0.0)
     return kmean, pmean, nmodes.astype(np.int64)
+
+
+def n_max(rho):
+    """eq. nmax: n_max = (2/3) rho / sqrt(1 - rho^2) (App. B; +inf at rho = 1)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return (2.0 / 3.0) * rho / np.sqrt(1.0 - rho * rho)
+
+
+def cross_correlation(delta_a, delta_b, box, nbins):
+    """Cross-correlation coefficient of two density meshes (Sec. 3.1) and n_max (eq. nmax).
+
+    rho(k) = <delta_a delta_b^*> / sqrt(<|delta_a|^2> <|delta_b|^2>), the ensemble averages
+    replaced by averages over the shells of power_spectrum (reading: the square root in the
+    denominator, as in App. B; the real part of the cross term, which is what the Hermitian
+    pairs +-k sum to).  The CIC window cancels in rho; the spectra are deconvolved as in
+    power_spectrum.  Returns (k, P_a, P_b, P_ab, rho, n_max, nmodes) for shells b = 1..nbins."""
+    ng = delta_a.shape[0]
+    da = scipy.fft.rfftn(np.asarray(delta_a, dtype=np.float64), workers=FFT_WORKERS)
+    db = scipy.fft.rfftn(np.asarray(delta_b, dtype=np.float64), workers=FFT_WORKERS)
+    nz, ny, nx = mode_numbers(ng)
+    m = np.broadcast_to(nx * nx + ny * ny + nz * nz, da.shape)
+    b = shell_index(m)
+    weight = np.broadcast_to(np.where((nx == 0) | (nx == ng // 2), 1.0, 2.0), da.shape)
+    norm = box**3 / float(ng) ** 6 / cic_window(ng) ** 2
+    sel = (b >= 1) & (b <= nbins)
+    idx = (b[sel] - 1).ravel()
+    w = weight[sel].ravel()
+
+    def shell_mean(q):
+        s = np.bincount(idx, weights=w * np.broadcast_to(q, da.shape)[sel].ravel(), minlength=nbins)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return np.where(nmodes > 0, s / nmodes, 0.0)
+
+    nmodes = np.bincount(idx, weights=w, minlength=nbins)
+    kmean = shell_mean(2.0 * np.pi / box * np.sqrt(m.astype(np.float64)))
+    pa = shell_mean(np.abs(da) ** 2 * norm)
+    pb = shell_mean(np.abs(db) ** 2 * norm)
+    pab = shell_mean((da * np.conj(db)).real * norm)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rho = pab / np.sqrt(pa * pb)
+    return kmean, pa, pb, pab, rho, n_max(rho), nmodes.astype(np.int64)

@@ -101,3 +101,38 @@ def test_power_single_mode():
     w = np.prod([np.sinc(m / n) ** 2 for m in modes])
     assert p[b - 1] == pytest.approx(2 * box**3 * amp**2 / 4 / w**2 / nm[b - 1], rel=1e-12)
     assert np.allclose(np.delete(p, b - 1), 0.0, atol=1e-20)
+
+
+def test_cross_correlation_limits_and_power_consistency():
+    from oracle import power
+    rng = np.random.default_rng(9)
+    n, box = 16, 40.0
+    d = rng.standard_normal((n, n, n))
+    e = rng.standard_normal((n, n, n))
+    k, pa, pb, pab, rho, nm, cnt = power.cross_correlation(d, d, box, 6)
+    k0, p0, c0 = power.power_spectrum(d, box, 6)
+    assert np.allclose(pa, p0, rtol=1e-12) and np.allclose(pab, p0, rtol=1e-12) and np.array_equal(cnt, c0)
+    assert np.allclose(rho, 1.0, rtol=0, atol=1e-12)
+    _, _, _, _, rho_neg, _, _ = power.cross_correlation(d, -2.0 * d, box, 6)
+    assert np.allclose(rho_neg, -1.0, rtol=0, atol=1e-12)
+    _, pa2, pb2, pab2, rho2, _, _ = power.cross_correlation(d, e, box, 6)
+    _, pba2, _, pba_ab, _, _, _ = power.cross_correlation(e, d, box, 6)
+    assert np.allclose(pab2, pba_ab, rtol=1e-12) and np.all(np.abs(rho2) < 1.0)
+
+
+def test_n_max_calibration_on_orthogonal_fields():
+    # App. B: with delta_NL = delta_M + eps, <delta_M eps*> = 0 and P_eps / P_NL = 10%, n_max = 2.
+    # delta_M = A cos(k.x) and eps = B sin(k.x) are orthogonal in every shell; B^2 / (A^2 + B^2)
+    # = 0.1 puts rho = sqrt(0.9) in the shell of k.
+    from oracle import power
+    n, box = 16, 40.0
+    i = np.arange(n)
+    z, y, x = np.meshgrid(i, i, i, indexing="ij")
+    ph = 2 * np.pi * (2 * x + 1 * y + 0 * z) / n  # |n|^2 = 5: shell 2
+    A, B = 3.0, 1.0
+    dm = A * np.cos(ph)
+    dnl = dm + B * np.sin(ph)
+    _, _, _, _, rho, nm, cnt = power.cross_correlation(dm, dnl, box, 4)
+    assert rho[1] == pytest.approx(np.sqrt(0.9), rel=1e-12)
+    assert nm[1] == pytest.approx(2.0, rel=1e-12)
+    assert power.n_max(np.sqrt(0.9)) == pytest.approx(2.0, rel=1e-14)
