@@ -184,6 +184,18 @@ int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta
 int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, double* pk,
                int64_t* nmodes, cola_stream stream);
 
+/* Cross-correlation of two density meshes (Sec. 3.1) and n_max (eq. nmax, App. B), for
+ * comparing a run with a reference run of the same initial conditions.  Per shell
+ * b = 1..nbins (the shells and weights of cola_power): k, P_a and P_b as cola_power,
+ * P_ab = (L^3/ng^6) Re(delta_a,k delta_b,k^*) / W(k)^2 averaged over the shell,
+ * rho = P_ab / sqrt(P_a P_b) (read with the square root, as App. B uses it) and
+ * nmax = (2/3) rho / sqrt(1 - rho^2) (+inf where rho = 1).  delta_a, delta_b: device float32
+ * [ng^3] (read only); k, pk_a, pk_b, pk_ab, rho, nmax: device float64 [nbins]; nmodes: device
+ * int64 [nbins].  nbins <= ng.  Deterministic (fixed reduction order). */
+int cola_cross_power(cola_plan* plan, const float* delta_a, const float* delta_b, int32_t nbins, double* k,
+                     double* pk_a, double* pk_b, double* pk_ab, double* rho, double* nmax, int64_t* nmodes,
+                     cola_stream stream);
+
 /* Forward 3-D real-to-complex DFT (exp(-i k.x), unscaled) of a real mesh of side n, where
  * n is the plan's ng (which = 0) or np (which = 1).  in: device float32 [n^3]; out: device
  * complex64 [n][n][n/2+1] (interleaved re, im). */

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "cola_density": [_P, _P, _P, _P, _P],
     "cola_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
+    "cola_cross_power": [_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P],
     "cola_status": [_P, _P],
     "cola_power_noalloc": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P],
     "cola_step_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
@@ -196,6 +197,12 @@ def cola_power_noalloc(delta, ng, box, nbins, k, pk, nmodes, stream=None):
     """P(k) of a density mesh (ng <= 128) with no plan, workspace or device allocation."""
     _check(load_library().cola_power_noalloc(_ptr(delta), int(ng), float(box), int(nbins), _ptr(k), _ptr(pk),
                                              _ptr(nmodes), _stream(stream)))
+
+
+def cola_cross_power(h, delta_a, delta_b, nbins, k, pk_a, pk_b, pk_ab, rho, nmax, nmodes, stream=None):
+    _check(load_library().cola_cross_power(h, _ptr(delta_a), _ptr(delta_b), int(nbins), _ptr(k), _ptr(pk_a),
+                                           _ptr(pk_b), _ptr(pk_ab), _ptr(rho), _ptr(nmax), _ptr(nmodes),
+                                           _stream(stream)))
 
 
 def cola_fft_r2c(h, which, x, out, stream=None):
@@ -375,6 +382,14 @@ class Plan:
         nm = self._empty(nbins, torch.int64)
         cola_power(self.handle, delta, nbins, k, pk, nm)
         return k, pk, nm
+
+    def cross_power(self, delta_a, delta_b, nbins):
+        """(k, P_a, P_b, P_ab, rho, n_max, nmodes) per shell (Sec. 3.1, eq. nmax)."""
+        _expect(delta_a, torch.float32, self.ng**3, "delta_a")
+        _expect(delta_b, torch.float32, self.ng**3, "delta_b")
+        out = [self._empty(nbins, torch.float64) for _ in range(6)] + [self._empty(nbins, torch.int64)]
+        cola_cross_power(self.handle, delta_a, delta_b, nbins, *out)
+        return tuple(out)
 
     def fft_r2c(self, x, which=0):
         n = self.ng if which == 0 else self.np

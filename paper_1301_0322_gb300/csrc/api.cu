@@ -355,6 +355,24 @@ int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, do
   return launch_power_finish(nbins, w.pk_partial, k, pk, nmodes, st);
 }
 
+int cola_cross_power(cola_plan* plan, const float* delta_a, const float* delta_b, int32_t nbins, double* k,
+                     double* pk_a, double* pk_b, double* pk_ab, double* rho, double* nmax, int64_t* nmodes,
+                     cola_stream stream) {
+  int rc = check_ws(plan);
+  if (rc) return rc;
+  ProfilerGuard pg(&plan->prof);
+  if (!delta_a || !delta_b || !k || !pk_a || !pk_b || !pk_ab || !rho || !nmax || !nmodes)
+    return fail(COLA_EINVAL, "null array");
+  if (nbins < 1 || nbins > plan->geo.ng) return fail(COLA_EINVAL, "nbins must be in [1, ng]");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& w = plan->ws;
+  if ((rc = fft3d_r2c(plan->geo.ng, plan->Pg, delta_a, w.meshA, w.tw_g, st))) return rc;
+  if ((rc = fft3d_r2c(plan->geo.ng, plan->Pg, delta_b, w.meshG[1], w.tw_g, st))) return rc;
+  if ((rc = launch_cross_bin(plan->geo.ng, plan->Pg, plan->cfg.box, nbins, w.meshA, w.meshG[1], w.pk_partial, st)))
+    return rc;
+  return launch_cross_finish(nbins, w.pk_partial, k, pk_a, pk_b, pk_ab, rho, nmax, nmodes, st);
+}
+
 int cola_fft_r2c(cola_plan* plan, int32_t which, const float* in, float* out, cola_stream stream) {
   int rc = check_ws(plan);
   if (rc) return rc;

@@ -169,6 +169,10 @@ constexpr int kPowerBlocks = 304;
 int power_partial_doubles(int nbins);  // size of the partial-sum buffer
 int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st);
 int launch_power_finish(int nbins, const double* partial, double* k, double* pk, int64_t* nmodes, cudaStream_t st);
+int launch_cross_bin(int ng, int P, double box, int nbins, const float2* da, const float2* db, double* partial,
+                     cudaStream_t st);
+int launch_cross_finish(int nbins, const double* partial, double* k, double* pa, double* pb, double* pab, double* rho,
+                        double* nmax, int64_t* nmodes, cudaStream_t st);
 int launch_unpad(int n, int P, const float2* in, float2* out, cudaStream_t st);
 
 }  // namespace cola

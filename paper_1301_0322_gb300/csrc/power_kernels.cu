@@ -24,16 +24,20 @@ __device__ __forceinline__ float sinc_pi_p(int n, int ng) {
 // the same shell are contiguous, so a segmented shuffle reduction (float32, at most 31 adds)
 // leaves each shell's sum in its first lane, which adds it in float64 to the warp's own
 // shared-memory accumulators (no atomics).  Each block then writes its per-shell totals in a
-// fixed order and k_power_finish adds the blocks in block order: the result is deterministic.
-// partial layout: [block][shell][3] = (sum w |k|, sum w P, sum w).
+// fixed order and the finish kernel adds the blocks in block order: the result is
+// deterministic.  NF = 1: one field, partial layout [block][shell][3] = (sum w |k|, sum w P,
+// sum w); NF = 2: two fields a, b, [block][shell][5] = (sum w |k|, sum w P_a, sum w P_b,
+// sum w P_ab, sum w) with P_ab from Re(a b^*).
+template <int NF>
 __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, const float2* __restrict__ dk,
-                            double* __restrict__ partial) {
+                            const float2* __restrict__ dk2, double* __restrict__ partial) {
+  constexpr int NQ = NF == 1 ? 3 : 5;
   extern __shared__ double pacc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nh = ng / 2 + 1;
-  for (int i = threadIdx.x; i < nwarps * nbins * 3; i += blockDim.x) pacc[i] = 0.0;
+  for (int i = threadIdx.x; i < nwarps * nbins * NQ; i += blockDim.x) pacc[i] = 0.0;
   __syncthreads();
-  double* mine = pacc + (size_t)warp * nbins * 3;
+  double* mine = pacc + (size_t)warp * nbins * NQ;
   const int64_t nrows = (int64_t)ng * ng;
   for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < nrows; row += (int64_t)gridDim.x * nwarps) {
     const int ky = (int)(row % ng), kz = (int)(row / ng);
@@ -42,50 +46,58 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
     const float sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
     const float wyz = (sy * sy) * (sz * sz);
     const float2* rowp = dk + row * P;
+    const float2* rowq = NF == 2 ? dk2 + row * P : nullptr;
     for (int c0 = 0; c0 < nh; c0 += 32) {
       const int kx = c0 + lane;
       int b = -1;
-      float kw = 0.f, pw = 0.f, w = 0.f;
+      float q[NQ];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) q[j] = 0.f;
       if (kx < nh) {
         const int m = kx * kx + myz;
         const int sb = shell_of(m);
         if (sb >= 1 && sb <= nbins) {
           b = sb - 1;
-          w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
+          const float w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
           const float2 d = rowp[kx];
           const float sx = sinc_pi_p(kx, ng);
           const float win = (sx * sx) * wyz;
-          kw = w * kf * sqrtf((float)m);
-          pw = w * (d.x * d.x + d.y * d.y) * pnorm / (win * win);
+          const float scale = w * pnorm / (win * win);
+          q[0] = w * kf * sqrtf((float)m);
+          q[1] = (d.x * d.x + d.y * d.y) * scale;
+          if constexpr (NF == 2) {
+            const float2 e = rowq[kx];
+            q[2] = (e.x * e.x + e.y * e.y) * scale;
+            q[3] = (d.x * e.x + d.y * e.y) * scale;
+          }
+          q[NQ - 1] = w;
         }
       }
       // segmented reduction toward the first lane of each run of equal shells
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int bo = __shfl_down_sync(0xffffffffu, b, o);
-        const float ko = __shfl_down_sync(0xffffffffu, kw, o);
-        const float po = __shfl_down_sync(0xffffffffu, pw, o);
-        const float wo = __shfl_down_sync(0xffffffffu, w, o);
+        float qo[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) qo[j] = __shfl_down_sync(0xffffffffu, q[j], o);
         if (lane + o < 32 && bo == b) {
-          kw += ko;
-          pw += po;
-          w += wo;
+#pragma unroll
+          for (int j = 0; j < NQ; ++j) q[j] += qo[j];
         }
       }
       const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
       if (b >= 0 && (lane == 0 || bprev != b)) {
-        mine[3 * b] += (double)kw;
-        mine[3 * b + 1] += (double)pw;
-        mine[3 * b + 2] += (double)w;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) mine[NQ * b + j] += (double)q[j];
       }
       __syncwarp();
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nbins * 3; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nbins * NQ; i += blockDim.x) {
     double t = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) t += pacc[(size_t)wv * nbins * 3 + i];
-    partial[(size_t)blockIdx.x * nbins * 3 + i] = t;
+    for (int wv = 0; wv < nwarps; ++wv) t += pacc[(size_t)wv * nbins * NQ + i];
+    partial[(size_t)blockIdx.x * nbins * NQ + i] = t;
   }
 }
 
@@ -105,6 +117,31 @@ __global__ void k_power_finish(int nbins, int nblocks, const double* __restrict_
   nmodes[b] = (int64_t)cs;
 }
 
+// shell means of the two spectra and the cross term, rho = P_ab / sqrt(P_a P_b) (Sec. 3.1) and
+// n_max = (2/3) rho / sqrt(1 - rho^2) (eq. nmax)
+__global__ void k_cross_finish(int nbins, int nblocks, const double* __restrict__ partial, double* __restrict__ k,
+                               double* __restrict__ pa, double* __restrict__ pb, double* __restrict__ pab,
+                               double* __restrict__ rho, double* __restrict__ nmax, int64_t* __restrict__ nmodes) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int blk = 0; blk < nblocks; ++blk) {
+    const double* r = partial + ((size_t)blk * nbins + b) * 5;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) s[j] += r[j];
+  }
+  const double cs = s[4];
+  const double ma = cs > 0 ? s[1] / cs : 0.0, mb = cs > 0 ? s[2] / cs : 0.0, mab = cs > 0 ? s[3] / cs : 0.0;
+  const double r = mab / sqrt(ma * mb);
+  k[b] = cs > 0 ? s[0] / cs : 0.0;
+  pa[b] = ma;
+  pb[b] = mb;
+  pab[b] = mab;
+  rho[b] = r;
+  nmax[b] = (2.0 / 3.0) * r / sqrt(1.0 - r * r);
+  nmodes[b] = (int64_t)cs;
+}
+
 __global__ void k_unpad(int n, int P, const float2* __restrict__ in, float2* __restrict__ out) {
   const int nh = n / 2 + 1;
   const int64_t total = (int64_t)n * n * nh;
@@ -114,24 +151,48 @@ __global__ void k_unpad(int n, int P, const float2* __restrict__ in, float2* __r
   }
 }
 
-static int power_warps(int nbins) {
-  const int w = (int)((160 * 1024) / ((size_t)nbins * 3 * sizeof(double)));
+static int power_warps(int nbins, int nq) {
+  const int w = (int)((160 * 1024) / ((size_t)nbins * nq * sizeof(double)));
   return std::max(1, std::min(8, w));
 }
 
-int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * 3; }
+int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * 5; }
 
-int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st) {
+template <int NF>
+static int power_bin_t(int ng, int P, double box, int nbins, const float2* dk, const float2* dk2, double* partial,
+                       cudaStream_t st) {
+  constexpr int NQ = NF == 1 ? 3 : 5;
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const double ng6 = std::pow((double)ng, 6.0);
   const float pnorm = (float)(box * box * box / ng6);
-  const int warps = power_warps(nbins);
-  const size_t smem = (size_t)warps * nbins * 3 * sizeof(double);
+  const int warps = power_warps(nbins, NQ);
+  const size_t smem = (size_t)warps * nbins * NQ * sizeof(double);
+  if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "power spectrum: too many bins for shared memory");
   if (smem > 32 * 1024)
-    COLA_CUDA_CHECK(cudaFuncSetAttribute(k_power_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    COLA_CUDA_CHECK(cudaFuncSetAttribute(k_power_bin<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
-    LaunchScope ls_("power_bin", st);
-    k_power_bin<<<kPowerBlocks, 32 * warps, smem, st>>>(ng, P, kf, pnorm, nbins, dk, partial);
+    LaunchScope ls_(NF == 1 ? "power_bin" : "cross_bin", st);
+    k_power_bin<NF><<<kPowerBlocks, 32 * warps, smem, st>>>(ng, P, kf, pnorm, nbins, dk, dk2, partial);
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st) {
+  return power_bin_t<1>(ng, P, box, nbins, dk, nullptr, partial, st);
+}
+
+int launch_cross_bin(int ng, int P, double box, int nbins, const float2* da, const float2* db, double* partial,
+                     cudaStream_t st) {
+  return power_bin_t<2>(ng, P, box, nbins, da, db, partial, st);
+}
+
+int launch_cross_finish(int nbins, const double* partial, double* k, double* pa, double* pb, double* pab, double* rho,
+                        double* nmax, int64_t* nmodes, cudaStream_t st) {
+  {
+    LaunchScope ls_("cross_finish", st);
+    k_cross_finish<<<(nbins + 127) / 128, 128, 0, st>>>(nbins, kPowerBlocks, partial, k, pa, pb, pab, rho, nmax,
+                                                         nmodes);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
