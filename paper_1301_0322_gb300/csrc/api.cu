@@ -38,6 +38,7 @@ static size_t layout(cola_plan* p, char* base) {
   w.err = (int*)take(sizeof(int) * 4);
   w.keys = (int*)take(sizeof(int) * np3);
   w.idx = (unsigned*)take(sizeof(unsigned) * np3);
+  w.coords = (uint32_t*)take(sizeof(uint32_t) * 3 * np3);
   w.counts = (int*)take(sizeof(int) * p->tiles.nbins);
   w.offsets = (int*)take(sizeof(int) * (p->tiles.nbins + 1));
   w.cursor = (int*)take(sizeof(int) * p->tiles.nbins);
@@ -77,7 +78,7 @@ static int bin_particles(cola_plan* p, const float* s, cudaStream_t st) {
   if (rc) return rc;
   rc = launch_scan(p->tiles, w.counts, w.offsets, w.cursor, w.scan_blocks, st);
   if (rc) return rc;
-  return launch_scatter(p->geo, w.keys, w.cursor, w.idx, st);
+  return launch_scatter(p->geo, s, w.keys, w.cursor, w.idx, w.coords, st);
 }
 
 // unit force meshes g_j (freal[j]) for positions s
@@ -85,7 +86,7 @@ static int force_meshes(cola_plan* p, const float* s, cudaStream_t st) {
   Workspace& w = p->ws;
   int rc = bin_particles(p, s, st);
   if (rc) return rc;
-  return launch_force_passes(p->geo, p->tiles, s, w.idx, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
+  return launch_force_passes(p->geo, p->tiles, w.coords, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
                              p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
 }
 

@@ -56,6 +56,7 @@ struct Workspace {
   // particle binning
   int* keys = nullptr;
   unsigned* idx = nullptr;
+  uint32_t* coords = nullptr;  // [3][np^3] fixed-point CIC coordinates in bin order
   int* counts = nullptr;    // nbins
   int* offsets = nullptr;   // nbins + 1
   int* cursor = nullptr;    // nbins
@@ -120,14 +121,15 @@ int fft3d_c2r(int n, int P, float2* in_destroyed, float* out, const float2* tw, 
 int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st);
 int scan_block_count(const Tiles& t);
 int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* block_sums, cudaStream_t st);
-int launch_scatter(const Geometry& g, const int* keys, int* cursor, unsigned* idx, cudaStream_t st);
+int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, unsigned* idx, uint32_t* coords,
+                   cudaStream_t st);
 int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
                    int64_t* rho, float* delta, int* err, cudaStream_t st);
 int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
                         cudaStream_t st);
 // the fused mesh passes of one force evaluation (pm_fft_kernels.cu): deposit + x r2c, y pass,
 // z pass with the Green's function, inverse y passes, inverse x passes -> F [3][ng^3]
-int launch_force_passes(const Geometry& g, const Tiles& tl, const float* s, const unsigned* idx, const int* offsets,
+int launch_force_passes(const Geometry& g, const Tiles& tl, const uint32_t* coords, const int* offsets,
                         float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv, const float2* tw,
                         int* err, cudaStream_t st);
 // mode 0: kick + drift, 1: kick + L+ (last force evaluation), 2: write the gathered unit force to gout

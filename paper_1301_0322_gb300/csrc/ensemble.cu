@@ -80,58 +80,57 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_keys(const BoxDesc* __restric
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
-                                                 int nbox, const int* __restrict__ keys, int* __restrict__ cursor,
-                                                 unsigned* __restrict__ idx) {
+__global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __restrict__ boxes,
+                                                           const int* __restrict__ starts, int nbox,
+                                                           const float* __restrict__ s, const int* __restrict__ keys,
+                                                           int* __restrict__ cursor, unsigned* __restrict__ idx,
+                                                           uint32_t* __restrict__ coords, int64_t cstride) {
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int b = find_box(starts, nbox, item);
     const BoxDesc& d = boxes[b];
     const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
-    scatter_body(p, p < d.g.np3, keys + d.pbase, cursor, idx);
+    scatter_body(d.g, s + 3 * d.pbase, p, p < d.g.np3, keys + d.pbase, cursor, idx, coords, cstride);
   }
 }
 
 // One tile of one box.  Not inlined: every (size, tile) instantiation gets its own register
 // allocation instead of the union of all of them.
 template <int N, int TY, int TZ>
-__device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const float* __restrict__ s,
-                                          const unsigned* __restrict__ idx, const int* __restrict__ offsets,
-                                          int tile) {
+__device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const uint32_t* __restrict__ coords,
+                                          int64_t cstride, const int* __restrict__ offsets, int tile) {
   extern __shared__ __align__(16) unsigned long long ens_smem[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ>(d->g, d->tl, s, idx, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile, ens_smem,
-                               ints);
+  deposit_fftx_body<N, TY, TZ>(d->g, d->tl, coords, cstride, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile,
+                               ens_smem, ints);
 }
 
 template <int N, int NT>
-__device__ __forceinline__ void deposit_item(const BoxDesc* d, const float* s, const unsigned* idx,
+__device__ __forceinline__ void deposit_item(const BoxDesc* d, const uint32_t* coords, int64_t cstride,
                                              const int* offsets, int tile) {
   constexpr int ROWS = NT / FFTConf<N / 2>::T;
   constexpr int TY0 = ens_tile_ty(ROWS, 0), TY1 = ens_tile_ty(ROWS, 1);
   if (d->tl.ty == TY0)
-    deposit_tile<N, TY0, ROWS / TY0>(d, s, idx, offsets, tile);
+    deposit_tile<N, TY0, ROWS / TY0>(d, coords, cstride, offsets, tile);
   else
-    deposit_tile<N, TY1, ROWS / TY1>(d, s, idx, offsets, tile);
+    deposit_tile<N, TY1, ROWS / TY1>(d, coords, cstride, offsets, tile);
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __restrict__ boxes,
                                                            const int* __restrict__ starts, int nbox,
-                                                           const float* __restrict__ s,
-                                                           const unsigned* __restrict__ idx,
+                                                           const uint32_t* __restrict__ coords, int64_t cstride,
                                                            const int* __restrict__ offsets) {
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int b = find_box(starts, nbox, item);
     const BoxDesc* d = boxes + b;
     const int local = item - __ldg(starts + b);
-    const float* sb = s + 3 * d->pbase;
     const int* ob = offsets + d->bin_base;
     switch (d->g.ng) {
-#define X(N)                                         \
-  case N:                                            \
-    deposit_item<N, NT>(d, sb, idx, ob, local);      \
+#define X(N)                                              \
+  case N:                                                 \
+    deposit_item<N, NT>(d, coords, cstride, ob, local);   \
     break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -310,6 +309,7 @@ struct cola_ensemble {
   // shared device buffers
   int* keys = nullptr;
   unsigned* idx = nullptr;
+  uint32_t* coords = nullptr;  // [3][all particles] fixed-point CIC coordinates in bin order
   int* counts = nullptr;
   int* offsets = nullptr;
   int* cursor = nullptr;
@@ -455,12 +455,14 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   if (rc) return rc;
   {
     LaunchScope ls_("ens_scatter", st);
-    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, e->keys, e->cursor, e->idx);
+    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->cursor, e->idx, e->coords,
+                                                        e->poff[nb]);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_deposit_fftx", st);
-    ke_deposit<NT><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, s, e->idx, e->offsets);
+    ke_deposit<NT><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->coords, e->poff[nb],
+                                                                        e->offsets);
   }
   COLA_LAUNCH_CHECK();
   {
@@ -578,6 +580,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
   all.nbins = e->max_bins_total;
   off += align256(sizeof(int) * np_all);                   // keys
   off += align256(sizeof(unsigned) * np_all);              // idx
+  off += align256(sizeof(uint32_t) * 3 * np_all);          // coords
   off += align256(sizeof(int) * all.nbins);                // counts
   off += align256(sizeof(int) * (all.nbins + 1));          // offsets
   off += align256(sizeof(int) * all.nbins);                // cursor
@@ -623,6 +626,7 @@ int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes,
   all.nbins = ens->max_bins_total;
   ens->keys = (int*)take(sizeof(int) * np_all);
   ens->idx = (unsigned*)take(sizeof(unsigned) * np_all);
+  ens->coords = (uint32_t*)take(sizeof(uint32_t) * 3 * np_all);
   ens->counts = (int*)take(sizeof(int) * all.nbins);
   ens->offsets = (int*)take(sizeof(int) * (all.nbins + 1));
   ens->cursor = (int*)take(sizeof(int) * all.nbins);

@@ -39,9 +39,13 @@ __device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, co
   if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
-// Counting-sort scatter: idx[cursor[keys[p]]++] = p, one atomic per distinct key in the warp.
-__device__ __forceinline__ void scatter_body(int64_t p, bool live, const int* __restrict__ keys,
-                                             int* __restrict__ cursor, unsigned* __restrict__ idx) {
+// Counting-sort scatter: pos = cursor[keys[p]]++ (one atomic per distinct key in the warp),
+// idx[pos] = p, and the particle's fixed-point CIC coordinates f_d = (cell << F) | t (x, y, z;
+// each < ng 2^F <= 2^31) at coords[d * cstride + pos], so the deposit reads them in bin order.
+__device__ __forceinline__ void scatter_body(const Geometry& g, const float* __restrict__ s, int64_t p, bool live,
+                                             const int* __restrict__ keys, int* __restrict__ cursor,
+                                             unsigned* __restrict__ idx, uint32_t* __restrict__ coords,
+                                             int64_t cstride) {
   const int key = live ? keys[p] : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
@@ -50,7 +54,19 @@ __device__ __forceinline__ void scatter_body(int64_t p, bool live, const int* __
   if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
   base = __shfl_sync(peers, base, leader);
   const int rank = __popc(peers & ((1u << lane) - 1u));
-  if (live) idx[base + rank] = (unsigned)p;
+  if (live) {
+    const int pos = base + rank;
+    idx[pos] = (unsigned)p;
+    int ix, iy, iz;
+    lattice_index(g, p, ix, iy, iz);
+    const int li[3] = {ix, iy, iz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int c, t;
+      fixed_axis(g, li[d], s[d * g.np3 + p], c, t);
+      coords[d * cstride + pos] = ((uint32_t)c << g.fbits) | (uint32_t)t;
+    }
+  }
 }
 
 // CIC gather of the three force meshes fmesh [3][ng^3] at particle p (the deposit's weights),

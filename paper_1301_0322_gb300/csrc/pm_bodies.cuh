@@ -47,12 +47,13 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
 // ---- 1. deposit + x r2c -----------------------------------------------------------------------
 // block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
 // bytes of shared memory; ints: 28 ints of shared memory
+// coords: [3][cstride] fixed-point CIC coordinates in bin order (offsets index them directly)
 template <int N, int TY, int TZ>
-__device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s,
-                                                  const unsigned* __restrict__ idx, const int* __restrict__ offsets,
-                                                  float2* __restrict__ out, int P, const float2* __restrict__ tw,
-                                                  float dscale, int* __restrict__ err, int tile,
-                                                  unsigned long long* acc, int* ints) {
+__device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl,
+                                                  const uint32_t* __restrict__ coords, int64_t cstride,
+                                                  const int* __restrict__ offsets, float2* __restrict__ out, int P,
+                                                  const float2* __restrict__ tw, float dscale, int* __restrict__ err,
+                                                  int tile, unsigned long long* acc, int* ints) {
   constexpr int M = N / 2, T = FFTConf<M>::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS;
   int* rbeg = ints;
   int* rpre = ints + 9;
@@ -86,36 +87,30 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   const int total = rpre[9];
   const unsigned long long one = 1ull << g.fbits;
   constexpr int U = 4;  // particles in flight per thread
+  const uint32_t fmask = (uint32_t)one - 1u;
   for (int base = threadIdx.x; base < total; base += NT * U) {
-    int64_t pp[U];
-    float sv[U][3];
+    uint32_t f[U][3];
+    bool ok[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * NT;
-      pp[u] = -1;
-      if (i < total) {
+      ok[u] = i < total;
+      if (ok[u]) {
         int r = 0;
 #pragma unroll
         for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
-        pp[u] = idx[rbeg[r] + (i - rpre[r])];
+        const int64_t pos = rbeg[r] + (i - rpre[r]);
+        f[u][0] = __ldg(coords + pos);
+        f[u][1] = __ldg(coords + cstride + pos);
+        f[u][2] = __ldg(coords + 2 * cstride + pos);
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (pp[u] >= 0) {
-        sv[u][0] = s[pp[u]];
-        sv[u][1] = s[g.np3 + pp[u]];
-        sv[u][2] = s[2 * g.np3 + pp[u]];
-      }
-#pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (pp[u] < 0) continue;
-      int ix, iy, iz;
-      lattice_index(g, pp[u], ix, iy, iz);
-      int cx, tx, cy, ty, cz, tz;
-      fixed_axis(g, ix, sv[u][0], cx, tx);
-      fixed_axis(g, iy, sv[u][1], cy, ty);
-      fixed_axis(g, iz, sv[u][2], cz, tz);
+      if (!ok[u]) continue;
+      const int cx = (int)(f[u][0] >> g.fbits), tx = (int)(f[u][0] & fmask);
+      const int cy = (int)(f[u][1] >> g.fbits), ty = (int)(f[u][1] & fmask);
+      const int cz = (int)(f[u][2] >> g.fbits), tz = (int)(f[u][2] & fmask);
       const int cx1 = wrap_inc(cx, N);
       const unsigned long long wx0 = one - tx, wx1 = tx;
 #pragma unroll
@@ -183,17 +178,20 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
     auto store = [&](int n, float2 x) { S0[n * W + w] = x; };
     fft_1d<N, 1, false>(t, tw, load, mem, store);
   }
-  // sinc^2 table of the z index, then phi_k = delta_k g(k) in place in S0 (one pass)
+  // sinc^2 tables of the z index and of the block's W columns, then
+  // phi_k = delta_k norm / (k^2 W(k)^p) in place in S0 with one division per mode
   float* sz2 = reinterpret_cast<float*>(S1);  // S1 is free between the transforms
-  for (int n = threadIdx.x; n < N; n += NT) {
-    const float sz = sinc_pi_f(signed_mode(n, N), N);
-    sz2[n] = sz * sz;
+  float* sx2 = sz2 + N;
+  for (int n = threadIdx.x; n < N + W; n += NT) {
+    const float sv = n < N ? sinc_pi_f(signed_mode(n, N), N) : sinc_pi_f(bx * W + (n - N), N);
+    (n < N ? sz2[n] : sx2[n - N]) = sv * sv;
   }
   __syncthreads();
   {
     const int ny = signed_mode(ky, N);
     const float sy = sinc_pi_f(ny, N);
     const float wy = sy * sy;
+    const float kf2 = kf * kf;
     for (int i = threadIdx.x; i < N * W; i += NT) {
       const int n = i / W, c = i - n * W;
       const int nx = bx * W + c;
@@ -201,12 +199,12 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
       const int m2 = nx * nx + ny * ny + nz * nz;
       float gk = 0.0f;
       if (m2 != 0 && nx < nh) {
-        gk = norm / (kf * kf * (float)m2);
+        float den = kf2 * (float)m2;
         if (deconv) {
-          const float sx = sinc_pi_f(nx, N);
-          const float wk = (sx * sx) * wy * sz2[n];
-          gk /= (deconv == 2 ? wk * wk : wk);
+          const float wk = sx2[c] * wy * sz2[n];
+          den *= deconv == 2 ? wk * wk : wk;
         }
+        gk = norm / den;
       }
       S0[i] = c_scale(S0[i], gk);
     }

@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ co
   if (i == n - 1) offsets[n] = excl + x;
 }
 
-__global__ void k_scatter(int64_t np3, const int* __restrict__ keys, int* __restrict__ cursor,
-                          unsigned* __restrict__ idx) {
+__global__ void k_scatter(Geometry g, const float* __restrict__ s, const int* __restrict__ keys,
+                          int* __restrict__ cursor, unsigned* __restrict__ idx, uint32_t* __restrict__ coords) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  scatter_body(p, p < np3, keys, cursor, idx);
+  scatter_body(g, s, p, p < g.np3, keys, cursor, idx, coords, g.np3);
 }
 
 // ---- deposit ----------------------------------------------------------------------------------
@@ -253,9 +253,10 @@ int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* blo
   return COLA_OK;
 }
 
-int launch_scatter(const Geometry& g, const int* keys, int* cursor, unsigned* idx, cudaStream_t st) {
+int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, unsigned* idx, uint32_t* coords,
+                   cudaStream_t st) {
   { LaunchScope ls_("scatter", st);
-  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g.np3, keys, cursor, idx); }
+  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, s, keys, cursor, idx, coords); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
