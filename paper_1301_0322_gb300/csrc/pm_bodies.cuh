@@ -245,6 +245,9 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
   float2* b = B + slab;
   float2* gy = Gy + slab;
   float2* gz = Gz + slab;
+  // the Gz strip is read only by the third transform: start pulling it into L2 now
+  if (w == 0)
+    for (int n = t; n < N; n += T) prefetch_l2_line(Gz + (int64_t)z * N * P + bx * W + (int64_t)n * P);
   for (int n = t; n < N; n += T) S0[n * W + w] = valid ? b[(int64_t)n * P] : make_float2(0.f, 0.f);
   __syncthreads();
   auto mem = [&](int n) -> float2& { return S1[n * W + w]; };
