@@ -8,8 +8,8 @@ Readings of this library (the paper runs an external FOF code and gives no more 
   * positions are the fixed-point CIC coordinates of the particles (mesh cells x 2^F, the
     same quantised positions the PM force uses; oracle.mesh.fixed_point_coords);
   * two particles are friends iff their periodic minimum-image distance d satisfies
-    d < b s, s = (ng / np) 2^F the mean separation in those units; with b = 1/5 the test is
-    the integer comparison 25 d^2 < s^2 (exact, no rounding);
+    d < b s, s = (ng / np) 2^F the mean separation in those units; with b = num/den (1/5 in
+    the paper) the test is the integer comparison den^2 d^2 < num^2 s^2 (exact, no rounding);
   * groups are the connected components of the friendship graph; a group is labelled by the
     smallest particle index it contains; halos are groups of at least nmin particles;
   * the mass function is reported as the number of halos with at least N_k particles for
@@ -20,11 +20,12 @@ import scipy.sparse
 import scipy.sparse.csgraph
 
 
-def friend_pairs(f, period, s_fixed, chunk=2048):
-    """All pairs (i < j) with 25 |d|^2 < s^2 by brute force (int64), f: (3, n) int64."""
+def friend_pairs(f, period, s_fixed, b_num=1, b_den=5, chunk=2048):
+    """All pairs (i < j) with den^2 |d|^2 < num^2 s^2 by brute force (int64), f: (3, n) int64."""
     f = np.asarray(f, dtype=np.int64)
     n = f.shape[1]
-    lim = np.int64(s_fixed) * np.int64(s_fixed)
+    lim = np.int64(b_num) ** 2 * np.int64(s_fixed) * np.int64(s_fixed)
+    den2 = np.int64(b_den) ** 2
     out_i, out_j = [], []
     for a in range(0, n, chunk):
         fa = f[:, a:a + chunk]
@@ -33,7 +34,7 @@ def friend_pairs(f, period, s_fixed, chunk=2048):
             d = fa[ax][:, None] - f[ax][None, :]
             d = np.mod(d + period // 2, period) - period // 2  # minimum image
             d2 += d * d
-        ii, jj = np.nonzero(25 * d2 < lim)
+        ii, jj = np.nonzero(den2 * d2 < lim)
         ii = ii + a
         keep = ii < jj
         out_i.append(ii[keep])
@@ -41,11 +42,11 @@ def friend_pairs(f, period, s_fixed, chunk=2048):
     return np.concatenate(out_i), np.concatenate(out_j)
 
 
-def fof_groups(f, period, s_fixed, nmin):
+def fof_groups(f, period, s_fixed, nmin, b_num=1, b_den=5):
     """Returns (group, size): per particle, the smallest particle index of its FOF group if the
     group has at least nmin particles (else -1), and the size of its group."""
     n = f.shape[1]
-    i, j = friend_pairs(f, period, s_fixed)
+    i, j = friend_pairs(f, period, s_fixed, b_num, b_den)
     adj = scipy.sparse.coo_matrix((np.ones(i.size, dtype=np.int8), (i, j)), shape=(n, n))
     _, comp = scipy.sparse.csgraph.connected_components(adj, directed=False)
     first = np.full(comp.max() + 1, n, dtype=np.int64)
