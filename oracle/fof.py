@@ -20,10 +20,34 @@ import scipy.sparse
 import scipy.sparse.csgraph
 
 
-def friend_pairs(f, period, s_fixed, b_num=1, b_den=5, chunk=2048):
-    """All pairs (i < j) with den^2 |d|^2 < num^2 s^2 by brute force (int64), f: (3, n) int64."""
+def exact_friends(f, i, j, period, s_fixed, b_num, b_den):
+    """Keep the candidate pairs (i, j) that satisfy den^2 |d|^2 < num^2 s^2 (int64)."""
+    d2 = np.zeros(i.size, dtype=np.int64)
+    for ax in range(3):
+        d = f[ax][i] - f[ax][j]
+        d = np.mod(d + period // 2, period) - period // 2  # minimum image
+        d2 += d * d
+    keep = np.int64(b_den) ** 2 * d2 < np.int64(b_num) ** 2 * np.int64(s_fixed) * np.int64(s_fixed)
+    return i[keep], j[keep]
+
+
+def friend_pairs(f, period, s_fixed, b_num=1, b_den=5, chunk=2048, method="auto"):
+    """All pairs (i < j) with den^2 |d|^2 < num^2 s^2, f: (3, n) int64.
+
+    method "brute": every pair; "tree": candidates from a periodic k-d tree (scipy) within a
+    slightly larger float64 radius (a superset), then the same exact integer test; "auto"
+    uses the tree above 4096 particles."""
     f = np.asarray(f, dtype=np.int64)
     n = f.shape[1]
+    if method == "tree" or (method == "auto" and n > 4096):
+        import scipy.spatial
+        tree = scipy.spatial.cKDTree(f.T.astype(np.float64), boxsize=float(period))
+        r = float(s_fixed) * b_num / b_den * (1.0 + 1e-9) + 1.0
+        cand = tree.query_pairs(r, output_type="ndarray")
+        if cand.size == 0:
+            return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+        i, j = np.minimum(cand[:, 0], cand[:, 1]), np.maximum(cand[:, 0], cand[:, 1])
+        return exact_friends(f, i.astype(np.int64), j.astype(np.int64), period, s_fixed, b_num, b_den)
     lim = np.int64(b_num) ** 2 * np.int64(s_fixed) * np.int64(s_fixed)
     den2 = np.int64(b_den) ** 2
     out_i, out_j = [], []

@@ -86,3 +86,16 @@ def test_mass_function_counts_halos_above_thresholds():
     group = np.array([0, 0, 0, -1, 4, 4, -1])
     size = np.array([3, 3, 3, 1, 2, 2, 1])
     assert fof.mass_function(group, size, [1, 2, 3, 4]).tolist() == [2, 2, 1, 0]
+
+
+def test_tree_candidates_give_the_brute_force_pairs():
+    rng = np.random.default_rng(8)
+    centres = rng.integers(0, PERIOD, size=(3, 10))
+    pick = rng.integers(0, 10, size=3000)
+    f = (centres[:, pick] + rng.normal(0, 60000, size=(3, 3000)).astype(np.int64)) % PERIOD
+    f[:, :20] = np.array([[0], [5], [7]]) + np.arange(20) * 39321 * np.array([[1], [0], [0]])  # on the threshold
+    f %= PERIOD
+    for b in ((1, 5), (1, 4), (2, 7)):
+        bi, bj = fof.friend_pairs(f, PERIOD, S, *b, method="brute")
+        ti, tj = fof.friend_pairs(f, PERIOD, S, *b, method="tree")
+        assert set(zip(bi.tolist(), bj.tolist())) == set(zip(ti.tolist(), tj.tolist()))
