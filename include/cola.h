@@ -196,6 +196,21 @@ int cola_cross_power(cola_plan* plan, const float* delta_a, const float* delta_b
                      double* pk_a, double* pk_b, double* pk_ab, double* rho, double* nmax, int64_t* nmodes,
                      cola_stream stream);
 
+/* Friends-of-friends halo groups (Sec. 3.2: linking length 0.2, at least 25 particles) of the
+ * particles at displacements s (device float32 [3][np^3], read only).  Positions are the
+ * fixed-point CIC coordinates of the force (2^-F cell); two particles are friends iff their
+ * periodic minimum-image distance d satisfies d < b s_mean, s_mean = (ng/np) 2^F, b =
+ * b_num / b_den (1 <= b_num <= b_den <= 50; the paper's b = 1/5), tested exactly in integers
+ * (b_den^2 d^2 < b_num^2 s_mean^2), so the groups are unique.  Outputs (device, may be NULL
+ * but not both): group [np^3] int32 = the smallest particle index of the particle's group if
+ * the group has at least nmin particles, else -1; size [np^3] int32 = the size of its group.
+ * Mass function: n_ge (device int64 [nthr]) = the number of halos (groups >= nmin) with at
+ * least thresholds[k] (host int32 [nthr], nthr <= 32) particles.  Needs ng a multiple of np;
+ * uses the plan's mesh buffers as scratch (their contents are lost).  A union-find that runs
+ * out of retries latches COLA_ETIMEOUT for cola_status. */
+int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t b_den, int32_t nmin, int32_t* group,
+             int32_t* size, int32_t nthr, const int32_t* thresholds, int64_t* n_ge, cola_stream stream);
+
 /* Forward 3-D real-to-complex DFT (exp(-i k.x), unscaled) of a real mesh of side n, where
  * n is the plan's ng (which = 0) or np (which = 1).  in: device float32 [n^3]; out: device
  * complex64 [n][n][n/2+1] (interleaved re, im). */

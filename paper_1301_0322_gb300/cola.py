@@ -65,6 +65,7 @@ _SIGNATURES = {
     "cola_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
     "cola_cross_power": [_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P],
+    "cola_fof": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P],
     "cola_status": [_P, _P],
     "cola_power_noalloc": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P],
     "cola_step_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
@@ -203,6 +204,13 @@ def cola_cross_power(h, delta_a, delta_b, nbins, k, pk_a, pk_b, pk_ab, rho, nmax
     _check(load_library().cola_cross_power(h, _ptr(delta_a), _ptr(delta_b), int(nbins), _ptr(k), _ptr(pk_a),
                                            _ptr(pk_b), _ptr(pk_ab), _ptr(rho), _ptr(nmax), _ptr(nmodes),
                                            _stream(stream)))
+
+
+def cola_fof(h, s, b_num, b_den, nmin, group, size, thresholds, n_ge, stream=None):
+    thr = np.ascontiguousarray(thresholds if thresholds is not None else [], dtype=np.int32)
+    _check(load_library().cola_fof(h, _ptr(s), int(b_num), int(b_den), int(nmin), _ptr(group), _ptr(size),
+                                   int(thr.size), thr.ctypes.data_as(ctypes.c_void_p) if thr.size else None,
+                                   _ptr(n_ge), _stream(stream)))
 
 
 def cola_fft_r2c(h, which, x, out, stream=None):
@@ -390,6 +398,17 @@ class Plan:
         out = [self._empty(nbins, torch.float64) for _ in range(6)] + [self._empty(nbins, torch.int64)]
         cola_cross_power(self.handle, delta_a, delta_b, nbins, *out)
         return tuple(out)
+
+    def fof(self, s, nmin=25, b=(1, 5), thresholds=None):
+        """Friends-of-friends groups (Sec. 3.2): (group label per particle, group size per
+        particle, number of halos with at least thresholds[k] particles)."""
+        _expect(s, torch.float32, 3 * self.n3, "s")
+        group = self._empty(self.n3, torch.int32)
+        size = self._empty(self.n3, torch.int32)
+        thr = [] if thresholds is None else list(thresholds)
+        n_ge = self._empty(max(1, len(thr)), torch.int64)
+        cola_fof(self.handle, s, b[0], b[1], nmin, group, size, thr, n_ge if thr else None)
+        return group, size, n_ge[:len(thr)]
 
     def fft_r2c(self, x, which=0):
         n = self.ng if which == 0 else self.np

@@ -151,3 +151,12 @@ def test_ensemble_create_validates_and_lays_out_the_boxes(lib):
     with pytest.raises(lib.ColaError) as e:
         lib.cola_ensemble_create([])
     assert e.value.code == 1
+
+
+def test_fof_needs_a_workspace(lib):
+    h = lib.cola_plan_create(lib.cola_config_default())
+    try:
+        cdll = lib.load_library()
+        assert cdll.cola_fof(h, None, 1, 5, 25, None, None, 0, None, None, None) == 5  # COLA_ENOWORKSPACE
+    finally:
+        lib.cola_plan_destroy(h)
