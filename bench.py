@@ -42,6 +42,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-fof", action="store_true")
     return ap.parse_args()
 
 
@@ -386,6 +387,28 @@ def gb300_arm(args):
         e2e = {"value": world * n3 * NSTEPS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": 4 * n3, "d2h_bytes_per_step": 2 * 12 * n3 + 8 * nbins}
 
+    # halo finding on the final state of the last run (Sec. 3.2: b = 0.2, >= 25 particles)
+    fof = None
+    if not args.no_fof and analysis and rank == 0:
+        thresholds = [25, 50, 100, 200, 400, 800, 1600, 3200]
+        group = plan._empty(n3, torch.int32)
+        size = plan._empty(n3, torch.int32)
+        n_ge = plan._empty(len(thresholds), torch.int64)
+        for _ in range(2):
+            cola.cola_fof(h, s, 1, 5, 25, group, size, thresholds, n_ge)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        cola.cola_fof(h, s, 1, 5, 25, group, size, thresholds, n_ge)
+        f1.record(stream)
+        f1.synchronize()
+        plan.status()
+        rho_crit = 2.775e11  # h^2 M_sun / Mpc^3
+        m_p = rho_crit * inputs.COSMOLOGY["omega_m"] * box**3 / n3
+        fof = {"ms": f0.elapsed_time(f1), "linking_length": 0.2, "nmin": 25, "particle_mass_msun_h": m_p,
+               "halos": int(n_ge[0]),
+               "n_ge": {f"{t * m_p:.3g}": int(c) for t, c in zip(thresholds, n_ge.tolist())},
+               "state": "final state of the last timed run"}
+
     # forward + adjoint on the differentiable workload, through the autograd wrapper
     fwd_adj = None
     del plan
@@ -421,7 +444,7 @@ def gb300_arm(args):
                        "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (meshes of several GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fwd_adjoint": fwd_adj,
-            "ensemble": ens,
+            "ensemble": ens, "fof": fof,
             "gpu_launches": int(cnt1.value - cnt0.value),
             "kernels": {kk: {"launches": kv["launches"], "ms_per_step": kv["ms"] / args.steps,
                              "share": round(kv["share"], 4)} for kk, kv in
