@@ -284,6 +284,10 @@ int cola_ensemble_workspace_bytes(const cola_ensemble* ens, size_t* bytes);
 int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes, cola_stream stream);
 /* Host arrays of nbox + 1 entries: poff (particle offsets) and moff (mesh-cell offsets). */
 int cola_ensemble_offsets(const cola_ensemble* ens, int64_t* poff, int64_t* moff);
+/* The four calls below and cola_ensemble_step run as CUDA graphs: recorded on the library's
+ * capture stream the first time they see a set of pointers (and seeds, nbins), replayed on
+ * `stream` afterwards (cola_ensemble_use_graphs(ens, 0) or profiling issues the launches
+ * directly). */
 /* Philox white noise of every box (cola_noise with seeds[b] into noise + poff[b]). */
 int cola_ensemble_noise(cola_ensemble* ens, const uint64_t* seeds, float* noise, cola_stream stream);
 /* 2LPT initial conditions of every box (cola_ic_2lpt on each box's slices). */

@@ -330,11 +330,11 @@ struct cola_ensemble {
   cudaStream_t cap = nullptr;
   struct Cached {
     cudaGraphExec_t exec = nullptr;
-    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<uintptr_t> key;  // pointers and scalars the recorded launches baked in
     int version = -1;
     unsigned long long kernels = 0;
   };
-  std::vector<Cached> graphs;
+  std::vector<Cached> graphs;  // one per step, then the noise, initial conditions, density, P(k)
   Profiler prof;
 
   ~cola_ensemble() {
@@ -525,6 +525,49 @@ bool valid_tuning(const cola_ensemble_tuning& t) {
          t.blocks_per_sm <= 64;
 }
 
+// Run `enqueue` on `st`: directly (graphs off or profiling), or as a CUDA graph recorded on
+// the private capture stream the first time these `key` values are seen, then replayed.
+template <class F>
+int replay(cola_ensemble* e, cola_ensemble::Cached& c, const std::vector<uintptr_t>& key, F&& enqueue,
+           cudaStream_t st) {
+  if (!e->use_graphs || e->prof.on) {
+    ProfilerGuard pg(&e->prof);
+    return enqueue(st);
+  }
+  if (!c.exec || c.version != e->version || c.key != key) {
+    if (c.exec) {
+      COLA_CUDA_CHECK(cudaGraphExecDestroy(c.exec));
+      c.exec = nullptr;
+    }
+    ProfilerGuard pg(nullptr);
+    const unsigned long long before = g_launches.load();
+    COLA_CUDA_CHECK(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeRelaxed));
+    const int rc = enqueue(e->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(e->cap, &graph);
+    const unsigned long long kernels = g_launches.load() - before;
+    g_launches.fetch_sub(kernels);  // counted when the graph runs
+    if (rc || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc ? rc : fail(COLA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&c.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      c.exec = nullptr;
+      return fail(COLA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    c.key = key;
+    c.version = e->version;
+    c.kernels = kernels;
+  }
+  COLA_CUDA_CHECK(cudaGraphLaunch(c.exec, st));
+  g_launches.fetch_add(c.kernels);
+  return COLA_OK;
+}
+
+uintptr_t u(const void* p) { return reinterpret_cast<uintptr_t>(p); }
+
 }  // namespace
 }  // namespace cola
 
@@ -588,7 +631,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
   off += align256(sizeof(BoxDesc) * nbox);                 // box descriptions
   off += align256(sizeof(int) * kENumLists * (nbox + 1));  // work lists
   e->ws_bytes = off;
-  e->graphs.resize(e->nsteps + 1);
+  e->graphs.resize(e->nsteps + 1 + 4);
   *out = e;
   return COLA_OK;
 }
@@ -653,9 +696,15 @@ int cola_ensemble_noise(cola_ensemble* ens, const uint64_t* seeds, float* noise,
   int rc = check_ens(ens);
   if (rc) return rc;
   if (!seeds || !noise) return fail(COLA_EINVAL, "null array");
-  for (int b = 0; b < ens->nbox; ++b)
-    if ((rc = cola_noise(ens->plans[b], seeds[b], noise + ens->poff[b], stream))) return rc;
-  return COLA_OK;
+  std::vector<uintptr_t> key{u(noise)};
+  for (int b = 0; b < ens->nbox; ++b) key.push_back((uintptr_t)seeds[b]);
+  return replay(ens, ens->graphs[ens->nsteps + 1], key, [&](cudaStream_t st) {
+    for (int b = 0; b < ens->nbox; ++b) {
+      const int r = cola_noise(ens->plans[b], seeds[b], noise + ens->poff[b], (cola_stream)st);
+      if (r) return r;
+    }
+    return (int)COLA_OK;
+  }, (cudaStream_t)stream);
 }
 
 int cola_ensemble_ic_2lpt(cola_ensemble* ens, const float* noise, float* s, float* v, float* s1, float* s2,
@@ -663,11 +712,14 @@ int cola_ensemble_ic_2lpt(cola_ensemble* ens, const float* noise, float* s, floa
   int rc = check_ens(ens);
   if (rc) return rc;
   if (!noise || !s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
-  for (int b = 0; b < ens->nbox; ++b) {
-    const int64_t o = ens->poff[b], o3 = 3 * ens->poff[b];
-    if ((rc = cola_ic_2lpt(ens->plans[b], noise + o, s + o3, v + o3, s1 + o3, s2 + o3, stream))) return rc;
-  }
-  return COLA_OK;
+  return replay(ens, ens->graphs[ens->nsteps + 2], {u(noise), u(s), u(v), u(s1), u(s2)}, [&](cudaStream_t st) {
+    for (int b = 0; b < ens->nbox; ++b) {
+      const int64_t o = ens->poff[b], o3 = 3 * ens->poff[b];
+      const int r = cola_ic_2lpt(ens->plans[b], noise + o, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)st);
+      if (r) return r;
+    }
+    return (int)COLA_OK;
+  }, (cudaStream_t)stream);
 }
 
 int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, const float* s1, const float* s2,
@@ -676,52 +728,22 @@ int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, con
   if (rc) return rc;
   if (!s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
   if (step < 0 || step > ens->nsteps) return fail(COLA_EINVAL, "step out of range");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!ens->use_graphs || ens->prof.on) {
-    ProfilerGuard pg(&ens->prof);
-    return enqueue_step_any(ens, step, s, v, s1, s2, st);
-  }
-  auto& c = ens->graphs[step];
-  const void* key[4] = {s, v, s1, s2};
-  if (!c.exec || c.version != ens->version || std::memcmp(c.key, key, sizeof(key)) != 0) {
-    if (c.exec) {
-      COLA_CUDA_CHECK(cudaGraphExecDestroy(c.exec));
-      c.exec = nullptr;
-    }
-    ProfilerGuard pg(nullptr);
-    const unsigned long long before = g_launches.load();
-    COLA_CUDA_CHECK(cudaStreamBeginCapture(ens->cap, cudaStreamCaptureModeRelaxed));
-    rc = enqueue_step_any(ens, step, s, v, s1, s2, ens->cap);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ens->cap, &graph);
-    const unsigned long long kernels = g_launches.load() - before;
-    g_launches.fetch_sub(kernels);  // counted when the graph runs
-    if (rc || ce != cudaSuccess || !graph) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc ? rc : fail(COLA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    }
-    const cudaError_t ie = cudaGraphInstantiate(&c.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) {
-      c.exec = nullptr;
-      return fail(COLA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
-    }
-    std::memcpy(c.key, key, sizeof(key));
-    c.version = ens->version;
-    c.kernels = kernels;
-  }
-  COLA_CUDA_CHECK(cudaGraphLaunch(c.exec, st));
-  g_launches.fetch_add(c.kernels);
-  return COLA_OK;
+  return replay(ens, ens->graphs[step], {u(s), u(v), u(s1), u(s2)},
+                [&](cudaStream_t st) { return enqueue_step_any(ens, step, s, v, s1, s2, st); },
+                (cudaStream_t)stream);
 }
 
 int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola_stream stream) {
   int rc = check_ens(ens);
   if (rc) return rc;
   if (!s || !delta) return fail(COLA_EINVAL, "null array");
-  for (int b = 0; b < ens->nbox; ++b)
-    if ((rc = cola_density(ens->plans[b], s + 3 * ens->poff[b], nullptr, delta + ens->moff[b], stream))) return rc;
-  return COLA_OK;
+  return replay(ens, ens->graphs[ens->nsteps + 3], {u(s), u(delta)}, [&](cudaStream_t st) {
+    for (int b = 0; b < ens->nbox; ++b) {
+      const int r = cola_density(ens->plans[b], s + 3 * ens->poff[b], nullptr, delta + ens->moff[b], (cola_stream)st);
+      if (r) return r;
+    }
+    return (int)COLA_OK;
+  }, (cudaStream_t)stream);
 }
 
 int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
@@ -730,11 +752,17 @@ int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, d
   if (rc) return rc;
   if (!delta || !k || !pk || !nmodes) return fail(COLA_EINVAL, "null array");
   if (nbins < 1 || nbins > ens->min_ng) return fail(COLA_EINVAL, "nbins must be in [1, smallest ng]");
-  for (int b = 0; b < ens->nbox; ++b) {
-    const size_t o = (size_t)b * nbins;
-    if ((rc = cola_power(ens->plans[b], delta + ens->moff[b], nbins, k + o, pk + o, nmodes + o, stream))) return rc;
-  }
-  return COLA_OK;
+  return replay(ens, ens->graphs[ens->nsteps + 4], {u(delta), (uintptr_t)nbins, u(k), u(pk), u(nmodes)},
+                [&](cudaStream_t st) {
+                  for (int b = 0; b < ens->nbox; ++b) {
+                    const size_t o = (size_t)b * nbins;
+                    const int r = cola_power(ens->plans[b], delta + ens->moff[b], nbins, k + o, pk + o, nmodes + o,
+                                             (cola_stream)st);
+                    if (r) return r;
+                  }
+                  return (int)COLA_OK;
+                },
+                (cudaStream_t)stream);
 }
 
 int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning) {
