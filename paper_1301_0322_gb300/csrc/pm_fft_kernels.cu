@@ -17,7 +17,7 @@ namespace cola {
 
 // ---- single-box kernels ------------------------------------------------------------------------
 template <int N, int TY, int TZ>
-__global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ)
+__global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, (512 / (FFTConf<N / 2>::T * TY * TZ)) > 0 ? 512 / (FFTConf<N / 2>::T * TY * TZ) : 1)
     k_deposit_fftx(Geometry g, Tiles tl, const uint32_t* __restrict__ coords, const int* __restrict__ offsets,
                    float2* __restrict__ out, int P, const float2* __restrict__ tw, float dscale,
                    int* __restrict__ err) {
