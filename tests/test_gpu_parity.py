@@ -232,3 +232,44 @@ def test_cross_power_matches_oracle(cola):
     # a field with itself
     _, _, _, _, rho_self, _, _ = (host(t) for t in plan.cross_power(deltas[0], deltas[0], nb))
     assert np.abs(rho_self - 1.0).max() <= 1e-12
+
+
+
+@pytest.mark.parametrize("fbits", [8, 12, 20])
+def test_deposit_bit_exact_other_fixed_point_widths(cola, fbits):
+    n_p, ng, box = 32, 64, 100.0
+    s = inputs.clustered_displacements(n_p, box, 6)
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, fixed_bits=fbits)
+    rho, _ = plan.density(dev(s), delta=False)
+    assert np.array_equal(host(rho).reshape(ng, ng, ng), omesh.cic_deposit_fixed(s, n_p, ng, box, fbits))
+    plan.status()
+
+
+def test_fixed_point_overflow_is_reported_by_both_deposits(cola):
+    # every particle on one node: 32^3 x 2^48 = 2^63 of integer weight, above the 2^62 guard
+    n_p, ng, box = 32, 64, 100.0
+    q = omesh.lattice_q(n_p, box)
+    s = (box / ng * 10.0 - q).astype(np.float32)  # every particle on node (10, 10, 10)
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box)
+    plan.density(dev(s), rho=True, delta=False)
+    with pytest.raises(cola.ColaError) as e:
+        plan.status()
+    assert e.value.code == 3
+    plan.force(dev(s))  # the fused deposit of the force path
+    with pytest.raises(cola.ColaError) as e:
+        plan.status()
+    assert e.value.code == 3
+    plan.status()
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_short_runs_match_oracle(cola, nsteps):
+    # one step: a single K-D-K plus the final kick and L+ (eq. ALCtimestep with n = 0)
+    n_p, ng, box = 32, 64, 100.0
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=nsteps)
+    w = inputs.gaussian_noise(n_p, 2)
+    s, v = gpu_run(cola, plan, w)
+    ref = ocola.run(w.reshape(n_p, n_p, n_p).astype(np.float64), ocola.ColaConfig(n_p=n_p, n_g=ng, box=box,
+                                                                                  nsteps=nsteps))
+    assert np.abs(host(s) - ref["s"]).max() / (box / ng) <= 1e-3
+    assert np.abs(host(v) - ref["v"]).max() <= 1e-3 * np.sqrt(np.mean(ref["v"] ** 2))
