@@ -42,11 +42,25 @@ class ColaConfig:
     a_final: float = 1.0
     deconv: int = 1
     spacing: str = "a"
+    fixed_bits: int = 0  # > 0: the force sees positions quantised to 2^-fixed_bits mesh cell
+
+
+def quantise_positions(pos, n_g, box, fbits):
+    """Positions rounded down to a multiple of 2^-fbits mesh cell (float64), periodic."""
+    scale = 2.0**fbits
+    u = np.floor(pos * (n_g / box) * scale) / scale
+    return np.mod(u, n_g) * (box / n_g)
 
 
 def acceleration(s, cfg, a):
-    """-(3/2) Om a d d^-2 delta at the particles (eq. eom), from the PM mesh of the config."""
+    """-(3/2) Om a d d^-2 delta at the particles (eq. eom), from the PM mesh of the config.
+
+    With cfg.fixed_bits = F > 0 the deposit and the gather see every position rounded down to a
+    multiple of 2^-F mesh cell (in float64), the quantisation the library's fixed-point CIC
+    applies; comparing against that run isolates the float32 rounding of the GPU path."""
     pos = np.mod(lattice_q(cfg.n_p, cfg.box) + s, cfg.box)
+    if cfg.fixed_bits > 0:
+        pos = quantise_positions(pos, cfg.n_g, cfg.box, cfg.fixed_bits)
     g = unit_force_particles(pos, cfg.n_p**3, cfg.n_g, cfg.box, cfg.deconv)
     return 1.5 * cfg.cosmo.omega_m * a * g
 

@@ -176,3 +176,19 @@ def test_axis_wave_reduction_equals_the_3d_force(n_p, ng, box, axis, m, deconv):
     scale = np.abs(ref).max()
     assert np.abs(g[axis] - ref[idx]).max() <= 1e-12 * scale
     assert np.abs(np.delete(g, axis, 0)).max() <= 1e-12 * scale
+
+
+
+def test_quantised_positions_deposit_the_fixed_point_density():
+    # displacements a fraction (0.1-0.9) of a quantum above a multiple of 2^-F cell: the float64
+    # rounding-down of oracle.cola.quantise_positions and the library's fixed-point coordinates
+    # agree, and the float64 CIC density of the quantised positions equals rho_fix / 2^3F
+    from oracle.cola import quantise_positions
+    n_p, ng, box, F = 8, 16, 16.0, 12  # H = 1 Mpc/h: cell units = Mpc/h
+    rng = np.random.default_rng(11)
+    k = rng.integers(-3000, 3000, size=(3, n_p**3))
+    s = ((k + rng.uniform(0.1, 0.9, size=k.shape)) / 2.0**F).astype(np.float32)
+    pos = np.mod(mesh.lattice_q(n_p, box) + s.astype(np.float64), box)
+    rho = mesh.cic_deposit(quantise_positions(pos, ng, box, F), ng, box)
+    fixed = mesh.cic_deposit_fixed(s, n_p, ng, box, F).astype(np.float64) / 2.0 ** (3 * F)
+    assert np.abs(rho - fixed).max() <= 1e-12 * fixed.max()
