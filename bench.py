@@ -275,12 +275,15 @@ def gb300_arm(args):
     lib = cola.load_library()
     n3 = n_p**3
     nbins = ng // 2
-    noise = plan._empty(n3)
-    s, v, s1, s2 = (plan._empty((3, n3)) for _ in range(4))
-    # the final density and P(k) need one more float mesh; at 2048^3 (34 GB) it does not fit
-    # next to the workspace and the particle state, so that workload stops at the last step
-    analysis = ng <= 1536
-    delta = plan._empty(ng**3) if analysis else None
+    s = plan._empty((3, n3))
+    # v, s1, s2 and the final density mesh share one allocation (the density is taken after the
+    # last step, when v, s1 and s2 are no longer read), and the noise sits in the v slot (the
+    # initial conditions transform it before they write v): at 1024^3/2048^3 this is what lets
+    # the density and P(k) fit beside the 215 GB workspace
+    pool = plan._empty(max(9 * n3, ng**3))
+    v, s1, s2 = (pool[i * 3 * n3:(i + 1) * 3 * n3].view(3, n3) for i in range(3))
+    noise = pool[:n3]
+    delta = pool[:ng**3]
     k, pk = plan._empty(nbins, torch.float64), plan._empty(nbins, torch.float64)
     nm = plan._empty(nbins, torch.int64)
 
@@ -289,9 +292,8 @@ def gb300_arm(args):
         cola.cola_ic_2lpt(h, noise, s, v, s1, s2)
         for i in range(NSTEPS + 1):
             cola.cola_step(h, i, s, v, s1, s2)
-        if analysis:
-            cola.cola_density(h, s, None, delta)
-            cola.cola_power(h, delta, nbins, k, pk, nm)
+        cola.cola_density(h, s, None, delta)
+        cola.cola_power(h, delta, nbins, k, pk, nm)
 
     base_seed = seed + 1000 * rank
     gpu_id = str(torch.cuda.get_device_properties(local).uuid)
@@ -353,7 +355,7 @@ def gb300_arm(args):
 
     # end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e and analysis:
+    if not args.no_e2e and ng <= 1536:  # pinned host copies of the 2048^3 state would be 30 GB
         h_noise = torch.empty(n3, dtype=torch.float32, pin_memory=True)
         h_s = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
         h_v = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
@@ -368,10 +370,10 @@ def gb300_arm(args):
             cola.cola_ic_2lpt(h, noise, s, v, s1, s2)
             for i in range(NSTEPS + 1):
                 cola.cola_step(h, i, s, v, s1, s2)
+            h_s.copy_(s, non_blocking=True)
+            h_v.copy_(v, non_blocking=True)  # before the density overwrites the v slot
             cola.cola_density(h, s, None, delta)
             cola.cola_power(h, delta, nbins, k, pk, nm)
-            h_s.copy_(s, non_blocking=True)
-            h_v.copy_(v, non_blocking=True)
             h_pk.copy_(pk, non_blocking=True)
 
         e2e_step()
@@ -389,7 +391,7 @@ def gb300_arm(args):
 
     # halo finding on the final state of the last run (Sec. 3.2: b = 0.2, >= 25 particles)
     fof = None
-    if not args.no_fof and analysis and rank == 0:
+    if not args.no_fof and rank == 0:
         thresholds = [25, 50, 100, 200, 400, 800, 1600, 3200]
         group = plan._empty(n3, torch.int32)
         size = plan._empty(n3, torch.int32)
@@ -440,7 +442,7 @@ def gb300_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "particles": f"{n_p}^3", "mesh": f"{ng}^3", "box_mpc_h": box,
-                       "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations" + (" + density + P(k)" if analysis else ""),
+                       "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations + density + P(k)",
                        "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (meshes of several GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fwd_adjoint": fwd_adj,
