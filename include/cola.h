@@ -262,17 +262,24 @@ typedef struct cola_ensemble cola_ensemble;
 /* Tunable launch shape of the ensemble kernels (chosen by cola_ensemble_tune):
  *  threads       block size of every persistent kernel, 128 or 256; it fixes the FFT
  *                columns per block (threads / (n / E)) and the deposit tile rows
- *  tile_shape    deposit tile (y x z rows) for a given row count: 0 = 4x4, 8x4, 8x8 for
- *                16, 32, 64 rows; 1 = 8x2, 4x8, 16x4.  Tiles are also the particle bins.
+ *  tile_shape    deposit tile (y x z rows) for a given row count: 0 = 4x2, 4x4, 8x4, 8x8,
+ *                16x8 for 8, 16, 32, 64, 128 rows; 1 = 2x4, 8x2, 4x8, 16x4, 8x16.  Tiles are
+ *                also the particle bins.
  *  blocks_per_sm persistent grid = blocks_per_sm x SM count, capped by occupancy; 0 = the
- *                occupancy limit. */
+ *                occupancy limit
+ *  radix         FFT factorisation of every transform length: 0 = the single-box one
+ *                (e.g. 256 = 16 x 16, 16 elements per thread), 1 = a second one with another
+ *                number of elements per thread (256 = 8 x 8 x 4, 8 per thread).  Variant 0
+ *                reproduces the single-box results bit for bit; variant 1 rounds differently
+ *                (same transforms, another order of operations). */
 typedef struct {
   int32_t threads;
   int32_t tile_shape;
   int32_t blocks_per_sm;
+  int32_t radix;
 } cola_ensemble_tuning;
 
-#define COLA_ENSEMBLE_TUNE_CANDIDATES 8
+#define COLA_ENSEMBLE_TUNE_CANDIDATES 16
 
 /* Create / destroy.  boxes: host array of nbox configurations (see the requirements above). */
 int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out);
@@ -309,7 +316,8 @@ int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, d
  * repetitions after one warm-up, CUDA events on `stream`; synchronises), keeps the fastest
  * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
  * milliseconds of each candidate, in the order threads in {128, 256} x tile_shape in {0, 1}
- * x blocks_per_sm in {0, 2}.  Every candidate gives bit-identical results. */
+ * x blocks_per_sm in {0, 2} x radix in {0, 1} (radix fastest).  Candidates with the same
+ * radix give bit-identical results. */
 int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
                        cola_stream stream);
 int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning);

@@ -60,9 +60,12 @@ __device__ __forceinline__ int find_box(const int* __restrict__ starts, int nbox
   return lo;
 }
 
-// rows of a deposit tile and its two shapes (tile_shape 0 / 1)
+// rows of a deposit tile (y) for a tile of `rows` rows and its two shapes (tile_shape 0 / 1):
+// 8 -> 4x2 / 2x4, 16 -> 4x4 / 8x2, 32 -> 8x4 / 4x8, 64 -> 8x8 / 16x4, 128 -> 16x8 / 8x16
 __host__ __device__ constexpr int ens_tile_ty(int rows, int shape) {
-  return shape == 0 ? (rows == 16 ? 4 : 8) : (rows == 16 ? 8 : (rows == 32 ? 4 : 16));
+  return rows == 8 ? (shape == 0 ? 4 : 2)
+                   : rows == 16 ? (shape == 0 ? 4 : 8)
+                                : rows == 32 ? (shape == 0 ? 8 : 4) : rows == 64 ? (shape == 0 ? 8 : 16) : (shape == 0 ? 16 : 8);
 }
 
 // ---- persistent kernels -----------------------------------------------------------------------
@@ -96,27 +99,28 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __rest
 
 // One tile of one box.  Not inlined: every (size, tile) instantiation gets its own register
 // allocation instead of the union of all of them.
-template <int N, int TY, int TZ>
+template <int N, int TY, int TZ, class CM>
 __device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const uint32_t* __restrict__ coords,
                                           int64_t cstride, const int* __restrict__ offsets, int tile) {
   extern __shared__ __align__(16) unsigned long long ens_smem[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ>(d->g, d->tl, coords, cstride, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile,
+  deposit_fftx_body<N, TY, TZ, CM>(d->g, d->tl, coords, cstride, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile,
                                ens_smem, ints);
 }
 
-template <int N, int NT>
+template <int N, int NT, int V>
 __device__ __forceinline__ void deposit_item(const BoxDesc* d, const uint32_t* coords, int64_t cstride,
                                              const int* offsets, int tile) {
-  constexpr int ROWS = NT / FFTConf<N / 2>::T;
+  using CM = FFTConfV<N / 2, V>;
+  constexpr int ROWS = NT / CM::T;
   constexpr int TY0 = ens_tile_ty(ROWS, 0), TY1 = ens_tile_ty(ROWS, 1);
   if (d->tl.ty == TY0)
-    deposit_tile<N, TY0, ROWS / TY0>(d, coords, cstride, offsets, tile);
+    deposit_tile<N, TY0, ROWS / TY0, CM>(d, coords, cstride, offsets, tile);
   else
-    deposit_tile<N, TY1, ROWS / TY1>(d, coords, cstride, offsets, tile);
+    deposit_tile<N, TY1, ROWS / TY1, CM>(d, coords, cstride, offsets, tile);
 }
 
-template <int NT>
+template <int NT, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __restrict__ boxes,
                                                            const int* __restrict__ starts, int nbox,
                                                            const uint32_t* __restrict__ coords, int64_t cstride,
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __rest
     switch (d->g.ng) {
 #define X(N)                                              \
   case N:                                                 \
-    deposit_item<N, NT>(d, coords, cstride, ob, local);   \
+    deposit_item<N, NT, V>(d, coords, cstride, ob, local); \
     break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __rest
 }
 
 // column passes: kind 0 = forward y, 1 = z with the Green's function, 2 = inverse y (three outputs)
-template <int NT, int KIND>
+template <int NT, int KIND, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
                                               int nbox) {
   extern __shared__ __align__(16) unsigned long long ens_smem[];
@@ -155,14 +159,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
     switch (d.g.ng) {
 #define X(N)                                                                                              \
   case N: {                                                                                               \
-    constexpr int W = NT / FFTConf<N>::T, nbx = (N / 2 + 1 + W - 1) / W;                                  \
+    using C = FFTConfV<N, V>;                                                                             \
+    constexpr int W = NT / C::T, nbx = (N / 2 + 1 + W - 1) / W;                                           \
     const int bx = local % nbx, slab = local / nbx;                                                       \
     if (KIND == 0)                                                                                        \
-      cols_body<N, W, false>(d.A, (int64_t)N * d.P, d.P, N / 2 + 1, d.tw, bx, slab, sm);                 \
+      cols_body<N, W, false, C>(d.A, (int64_t)N * d.P, d.P, N / 2 + 1, d.tw, bx, slab, sm);              \
     else if (KIND == 1)                                                                                   \
-      z_green_body<N, W>(d.A, d.Gz, d.P, d.kf, d.deconv, d.norm, d.tw, bx, slab, sm);                     \
+      z_green_body<N, W, C>(d.A, d.Gz, d.P, d.kf, d.deconv, d.norm, d.tw, bx, slab, sm);                  \
     else                                                                                                  \
-      y_inv3_body<N, W>(d.A, d.Gy, d.Gz, d.P, d.kf, d.tw, bx, slab, sm);                                  \
+      y_inv3_body<N, W, C>(d.A, d.Gy, d.Gz, d.P, d.kf, d.tw, bx, slab, sm);                               \
   } break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
 // Inverse x passes of all boxes: persistent, with the bulk copy of the next item (which may
 // belong to another box and mesh size) in flight during the transform of the current one.
 // half: float2 capacity of each of the two stage buffers.
-template <int NT>
+template <int NT, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restrict__ boxes,
                                                         const int* __restrict__ starts, int nbox, int half,
                                                         int* __restrict__ err) {
@@ -218,9 +223,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restric
     switch (d.g.ng) {
 #define X(N)                                                                                       \
   case N: {                                                                                        \
-    constexpr int RB = NT / FFTConf<N / 2>::T, nrb = N * N / RB;                                   \
+    using CM = FFTConfV<N / 2, V>;                                                                 \
+    constexpr int RB = NT / CM::T, nrb = N * N / RB;                                               \
     const int comp = local / nrb;                                                                  \
-    c2r3_compute<N, RB>(sm + buf * half, d.F + (int64_t)comp * N * N * N + (int64_t)(local - comp * nrb) * RB * N, \
+    c2r3_compute<N, RB, CM>(sm + buf * half, d.F + (int64_t)comp * N * N * N + (int64_t)(local - comp * nrb) * RB * N, \
                         comp, d.kf, d.tw);                                                         \
   } break;
       COLA_ENS_SIZES(X)
@@ -251,11 +257,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restr
 }
 
 // ---- host side ----------------------------------------------------------------------------------
-int host_T(int n) {
+// threads per transform of length n in radix variant v
+int host_T(int n, int v) {
   switch (n) {
 #define X(N) \
   case N:    \
-    return FFTConf<N>::T;
+    return v ? FFTConfV<N, 1>::T : FFTConfV<N, 0>::T;
     X(32) X(48) X(64) X(96) X(128) X(192) X(256)
 #undef X
     default:
@@ -280,11 +287,11 @@ struct Shape {
   int W, nbx, RB, rows, ty, tz;
 };
 
-Shape box_shape(int n, int nt, int tile_shape) {
+Shape box_shape(int n, int nt, int tile_shape, int v) {
   Shape s{};
-  s.W = nt / host_T(n);
+  s.W = nt / host_T(n, v);
   s.nbx = (n / 2 + 1 + s.W - 1) / s.W;
-  s.RB = nt / host_T(n / 2);
+  s.RB = nt / host_T(n / 2, v);
   s.rows = s.RB;
   s.ty = ens_tile_ty(s.rows, tile_shape);
   s.tz = s.rows / s.ty;
@@ -317,7 +324,7 @@ struct cola_ensemble {
   BoxDesc* d_boxes = nullptr;
   int* d_starts = nullptr;
   // current launch configuration
-  cola_ensemble_tuning tuning{256, 0, 0};
+  cola_ensemble_tuning tuning{256, 0, 0, 0};
   std::vector<BoxDesc> h_boxes;
   std::vector<int> h_starts;
   int total_bins = 0;
@@ -348,11 +355,12 @@ struct cola_ensemble {
 namespace cola {
 namespace {
 
-template <int NT>
+template <int NT, int V>
 int kernel_attrs(cola_ensemble* e) {
-  const void* fns[kKNum] = {(const void*)ke_keys<NT>,    (const void*)ke_scatter<NT>, (const void*)ke_deposit<NT>,
-                            (const void*)ke_cols<NT, 0>, (const void*)ke_cols<NT, 1>, (const void*)ke_cols<NT, 2>,
-                            (const void*)ke_c2r3<NT>,    (const void*)ke_gather<NT>};
+  const void* fns[kKNum] = {(const void*)ke_keys<NT>,       (const void*)ke_scatter<NT>,
+                            (const void*)ke_deposit<NT, V>, (const void*)ke_cols<NT, 0, V>,
+                            (const void*)ke_cols<NT, 1, V>, (const void*)ke_cols<NT, 2, V>,
+                            (const void*)ke_c2r3<NT, V>,    (const void*)ke_gather<NT>};
   const int lists[kKNum] = {kEParticles, kEParticles, kEDeposit, kECols, kECols, kECols, kEC2r, kEParticles};
   for (int k = 0; k < kKNum; ++k) {
     if (e->smem[k] > 227 * 1024) return fail(COLA_EUNSUPPORTED, "ensemble kernel: shared memory request too large");
@@ -378,7 +386,7 @@ int configure(cola_ensemble* e, cudaStream_t st) {
   for (int b = 0; b < nb; ++b) {
     cola_plan* p = e->plans[b];
     const int n = p->geo.ng;
-    const Shape sh = box_shape(n, nt, e->tuning.tile_shape);
+    const Shape sh = box_shape(n, nt, e->tuning.tile_shape, e->tuning.radix);
     BoxDesc& d = e->h_boxes[b];
     d.g = p->geo;
     d.tl.ty = sh.ty;
@@ -424,7 +432,9 @@ int configure(cola_ensemble* e, cudaStream_t st) {
   }
   if (bins > e->max_bins_total) return fail(COLA_EINVAL, "ensemble: bin count above the workspace sizing");
   e->total_bins = bins;
-  int rc = nt == 128 ? kernel_attrs<128>(e) : kernel_attrs<256>(e);
+  const int v = e->tuning.radix;
+  int rc = nt == 128 ? (v ? kernel_attrs<128, 1>(e) : kernel_attrs<128, 0>(e))
+                     : (v ? kernel_attrs<256, 1>(e) : kernel_attrs<256, 0>(e));
   if (rc) return rc;
   if (e->ws_base) {
     COLA_CUDA_CHECK(cudaMemcpyAsync(e->d_boxes, e->h_boxes.data(), sizeof(BoxDesc) * nb, cudaMemcpyHostToDevice, st));
@@ -437,7 +447,7 @@ int configure(cola_ensemble* e, cudaStream_t st) {
   return COLA_OK;
 }
 
-template <int NT>
+template <int NT, int V>
 int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   const int nb = e->nbox;
   const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
@@ -461,37 +471,37 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_deposit_fftx", st);
-    ke_deposit<NT><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->coords, e->poff[nb],
+    ke_deposit<NT, V><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->coords, e->poff[nb],
                                                                         e->offsets);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_y", st);
-    ke_cols<NT, 0><<<e->grid[kKYfwd], NT, e->smem[kKYfwd], st>>>(e->d_boxes, sc, nb);
+    ke_cols<NT, 0, V><<<e->grid[kKYfwd], NT, e->smem[kKYfwd], st>>>(e->d_boxes, sc, nb);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_z_green", st);
-    ke_cols<NT, 1><<<e->grid[kKZgreen], NT, e->smem[kKZgreen], st>>>(e->d_boxes, sc, nb);
+    ke_cols<NT, 1, V><<<e->grid[kKZgreen], NT, e->smem[kKZgreen], st>>>(e->d_boxes, sc, nb);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_y_inv3", st);
-    ke_cols<NT, 2><<<e->grid[kKYinv], NT, e->smem[kKYinv], st>>>(e->d_boxes, sc, nb);
+    ke_cols<NT, 2, V><<<e->grid[kKYinv], NT, e->smem[kKYinv], st>>>(e->d_boxes, sc, nb);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_x_c2r3", st);
     const int half = (int)(e->smem[kKC2r] / (2 * sizeof(float2)));
-    ke_c2r3<NT><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb, half, e->plans[0]->ws.err);
+    ke_c2r3<NT, V><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb, half, e->plans[0]->ws.err);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 
-template <int NT>
+template <int NT, int V>
 int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1, const float* s2, cudaStream_t st) {
-  int rc = enqueue_mesh_passes<NT>(e, s, st);
+  int rc = enqueue_mesh_passes<NT, V>(e, s, st);
   if (rc) return rc;
   const int nb = e->nbox;
   const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
@@ -506,12 +516,16 @@ int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1
 
 int enqueue_step_any(cola_ensemble* e, int step, float* s, float* v, const float* s1, const float* s2,
                      cudaStream_t st) {
-  return e->tuning.threads == 128 ? enqueue_step<128>(e, step, s, v, s1, s2, st)
-                                  : enqueue_step<256>(e, step, s, v, s1, s2, st);
+  const bool r = e->tuning.radix != 0;
+  if (e->tuning.threads == 128)
+    return r ? enqueue_step<128, 1>(e, step, s, v, s1, s2, st) : enqueue_step<128, 0>(e, step, s, v, s1, s2, st);
+  return r ? enqueue_step<256, 1>(e, step, s, v, s1, s2, st) : enqueue_step<256, 0>(e, step, s, v, s1, s2, st);
 }
 
 int enqueue_mesh_any(cola_ensemble* e, const float* s, cudaStream_t st) {
-  return e->tuning.threads == 128 ? enqueue_mesh_passes<128>(e, s, st) : enqueue_mesh_passes<256>(e, s, st);
+  const bool r = e->tuning.radix != 0;
+  if (e->tuning.threads == 128) return r ? enqueue_mesh_passes<128, 1>(e, s, st) : enqueue_mesh_passes<128, 0>(e, s, st);
+  return r ? enqueue_mesh_passes<256, 1>(e, s, st) : enqueue_mesh_passes<256, 0>(e, s, st);
 }
 
 int check_ens(const cola_ensemble* e) {
@@ -521,7 +535,8 @@ int check_ens(const cola_ensemble* e) {
 }
 
 bool valid_tuning(const cola_ensemble_tuning& t) {
-  return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) && t.blocks_per_sm >= 0 &&
+  return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) &&
+         (t.radix == 0 || t.radix == 1) && t.blocks_per_sm >= 0 &&
          t.blocks_per_sm <= 64;
 }
 
@@ -609,7 +624,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
     e->min_ng = std::min(e->min_ng, p->geo.ng);
     // most bins over the candidate launch shapes: the fewest tile rows (128 threads)
     const int n = p->geo.ng;
-    const int rows = 128 / host_T(n / 2);
+    const int rows = 128 / std::max(host_T(n / 2, 0), host_T(n / 2, 1));
     max_bins += 4LL * n * n / rows;
   }
   if (e->poff[nbox] >= 0x7fffffffLL || max_bins >= 0x7fffffffLL) {
@@ -800,7 +815,7 @@ int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_en
   double best_ms = 1e300;
   ProfilerGuard pg(nullptr);
   for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
-    ens->tuning = cola_ensemble_tuning{(i & 4) ? 256 : 128, (i >> 1) & 1, (i & 1) ? 2 : 0};
+    ens->tuning = cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1};
     if ((rc = configure(ens, st))) break;
     if ((rc = enqueue_mesh_any(ens, s, st))) break;  // warm-up
     if (cudaEventRecord(e0, st) != cudaSuccess) {

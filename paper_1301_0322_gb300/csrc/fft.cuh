@@ -162,6 +162,27 @@ COLA_FFT_CONF(1536, 24, 8, 8, 8, 3)
 COLA_FFT_CONF(2048, 16, 16, 16, 8)
 #undef COLA_FFT_CONF
 
+// Radix variants: FFTConfV<N, 0> is FFTConf<N>; FFTConfV<N, 1> is a second factorisation with a
+// different number of elements per thread (the ensemble autotuner times both).
+template <int N, int V>
+struct FFTConfV : FFTConf<N> {};
+#define COLA_FFT_ALT(N_, E_, ...)             \
+  template <>                                 \
+  struct FFTConfV<N_, 1> {                    \
+    static constexpr int N = N_;              \
+    static constexpr int E = E_;              \
+    static constexpr int T = N_ / E_;         \
+    using radices = Radices<__VA_ARGS__>;     \
+  };
+COLA_FFT_ALT(32, 4, 4, 4, 2)
+COLA_FFT_ALT(48, 24, 8, 6)
+COLA_FFT_ALT(64, 16, 16, 4)
+COLA_FFT_ALT(96, 12, 4, 4, 6)
+COLA_FFT_ALT(128, 8, 8, 4, 4)
+COLA_FFT_ALT(192, 12, 4, 4, 12)
+COLA_FFT_ALT(256, 8, 8, 8, 4)
+#undef COLA_FFT_ALT
+
 template <class L>
 struct FirstRadix;
 template <int R0, int... Rs>
@@ -245,9 +266,9 @@ struct Stockham {
 };
 
 // Convenience wrapper: load the first-stage inputs with load(n) and run the whole transform.
-template <int N, int TWS, bool INV, class Load, class Mem, class Store>
+template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store>
 __device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Load& load, Mem& mem, Store& store) {
-  using C = FFTConf<N>;
+  static_assert(C::N == N, "configuration of another length");
   constexpr int E = C::E, T = C::T;
   constexpr int R0 = FirstRadix<typename C::radices>::value;
   float2 v[E];

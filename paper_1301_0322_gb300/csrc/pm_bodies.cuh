@@ -29,7 +29,7 @@ __host__ __device__ constexpr int green_width() {
 
 // block (bx, slab): W columns of one slab of the in-place strided FFT (T(N) * W threads);
 // smem: N W float2.  Element (n, col) at data[slab * slab_stride + n * row_stride + col].
-template <int N, int W, bool INV>
+template <int N, int W, bool INV, class C = FFTConf<N>>
 __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride,
                                           int ncols, const float2* __restrict__ tw, int bx, int slab, float2* smem) {
   const int w = threadIdx.x % W, t = threadIdx.x / W;
@@ -41,20 +41,20 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
   auto store = [&](int n, float2 x) {
     if (valid) base[(int64_t)n * row_stride] = x;
   };
-  fft_1d<N, 1, INV>(t, tw, load, mem, store);
+  fft_1d<N, 1, INV, C>(t, tw, load, mem, store);
 }
 
 // ---- 1. deposit + x r2c -----------------------------------------------------------------------
 // block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
 // bytes of shared memory; ints: 28 ints of shared memory
 // coords: [3][cstride] fixed-point CIC coordinates in bin order (offsets index them directly)
-template <int N, int TY, int TZ>
+template <int N, int TY, int TZ, class CM = FFTConf<N / 2>>
 __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl,
                                                   const uint32_t* __restrict__ coords, int64_t cstride,
                                                   const int* __restrict__ offsets, float2* __restrict__ out, int P,
                                                   const float2* __restrict__ tw, float dscale, int* __restrict__ err,
                                                   int tile, unsigned long long* acc, int* ints) {
-  constexpr int M = N / 2, T = FFTConf<M>::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS;
+  constexpr int M = N / 2, T = CM::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS;
   int* rbeg = ints;
   int* rpre = ints + 9;
   int* rlen = ints + 19;
@@ -143,7 +143,7 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   };
   auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
   auto store = [&](int n, float2 x) { buf[xpad(n)] = x; };
-  fft_1d<M, 2, false>(t, tw, load, mem, store);
+  fft_1d<M, 2, false, CM>(t, tw, load, mem, store);
   if (overflow) atomicOr(err, kErrOverflow);
   __syncthreads();
   const int lz = w / TY, ly = w - lz * TY;
@@ -159,11 +159,11 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
 
 // ---- 3. z pass with the Green's function ------------------------------------------------------------
 // block (bx, ky): W columns kx of the slab ky (T(N) * W threads); sm: 2 N W float2
-template <int N, int W>
+template <int N, int W, class C = FFTConf<N>>
 __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __restrict__ Gz, int P, float kf,
                                              int deconv, float norm, const float2* __restrict__ tw, int bx, int ky,
                                              float2* sm) {
-  constexpr int nh = N / 2 + 1, NT = FFTConf<N>::T * W;
+  constexpr int nh = N / 2 + 1, NT = C::T * W;
   float2* S0 = sm;           // delta_k of the slab, [n][W]
   float2* S1 = sm + N * W;   // exchange buffer
   const int w = threadIdx.x % W, t = threadIdx.x / W;
@@ -176,7 +176,7 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
   {
     auto load = [&](int n) -> float2 { return valid ? a[n * zstride] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) { S0[n * W + w] = x; };
-    fft_1d<N, 1, false>(t, tw, load, mem, store);
+    fft_1d<N, 1, false, C>(t, tw, load, mem, store);
   }
   // sinc^2 tables of the z index and of the block's W columns, then
   // phi_k = delta_k norm / (k^2 W(k)^p) in place in S0 with one division per mode
@@ -215,7 +215,7 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
     auto store = [&](int n, float2 x) {
       if (valid) a[n * zstride] = x;
     };
-    fft_1d<N, 1, true>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 {
@@ -225,17 +225,17 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
     auto store = [&](int n, float2 x) {
       if (valid) gz[n * zstride] = x;
     };
-    fft_1d<N, 1, true>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }
 }
 
 // ---- 4. inverse y passes ------------------------------------------------------------------------------------
 // block (bx, z): W columns kx of the slab z (T(N) * W threads); sm: 2 N W float2
-template <int N, int W>
+template <int N, int W, class C = FFTConf<N>>
 __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz,
                                             int P, float kf, const float2* __restrict__ tw, int bx, int z,
                                             float2* sm) {
-  constexpr int nh = N / 2 + 1, T = FFTConf<N>::T;
+  constexpr int nh = N / 2 + 1, T = C::T;
   float2* S0 = sm;
   float2* S1 = sm + N * W;
   const int w = threadIdx.x % W, t = threadIdx.x / W;
@@ -256,7 +256,7 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
     auto store = [&](int n, float2 x) {
       if (valid) b[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 {
@@ -266,14 +266,14 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
     auto store = [&](int n, float2 x) {
       if (valid) gy[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 { return valid ? gz[(int64_t)n * P] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) gz[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }
 }
 
@@ -299,10 +299,10 @@ __device__ __forceinline__ void c2r3_issue(float2* stage, const float2* src_rows
 }
 
 // Inverse x transform of the staged rows into F rows (pitch N floats); comp 0 applies i k_x.
-template <int N, int RB>
+template <int N, int RB, class CM = FFTConf<N / 2>>
 __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ Frows, int comp, float kf,
                                              const float2* __restrict__ tw) {
-  constexpr int M = N / 2, T = FFTConf<M>::T, LD = xrow_ld<M>();
+  constexpr int M = N / 2, T = CM::T, LD = xrow_ld<M>();
   static_assert(T * RB <= 1024, "block too large");
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   float2* buf = stage + w * LD;
@@ -319,7 +319,7 @@ __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ 
   auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
   float2* dst = reinterpret_cast<float2*>(Frows + (int64_t)w * N);
   auto store = [&](int n, float2 x) { dst[n] = x; };
-  fft_1d<M, 2, true>(t, tw, load, mem, store);
+  fft_1d<M, 2, true, CM>(t, tw, load, mem, store);
 }
 
 }  // namespace cola

@@ -82,18 +82,29 @@ def run_steps(ens, seeds, nsteps):
 @pytest.mark.parametrize("threads", [128, 256])
 @pytest.mark.parametrize("tile_shape", [0, 1])
 @pytest.mark.parametrize("blocks_per_sm", [0, 2])
-def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, blocks_per_sm):
-    ens.tuning = (256, 0, 0)
+@pytest.mark.parametrize("radix", [0, 1])
+def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, blocks_per_sm, radix):
+    # radix variant 0 is the single-box factorisation: bit-identical; variant 1 factorises the
+    # transforms differently, so it agrees to float32 rounding (after two steps and the final
+    # kick: 1e-4 cell and 1e-4 of the rms velocity)
+    ens.tuning = (256, 0, 0, 0)
     ref_s, ref_v = run_steps(ens, SEEDS, 2)
-    ens.tuning = (threads, tile_shape, blocks_per_sm)
-    assert ens.tuning == (threads, tile_shape, blocks_per_sm)
+    ens.tuning = (threads, tile_shape, blocks_per_sm, radix)
+    assert ens.tuning == (threads, tile_shape, blocks_per_sm, radix)
     s, v = run_steps(ens, SEEDS, 2)
     ens.status()
-    assert torch.equal(s, ref_s) and torch.equal(v, ref_v)
+    if radix == 0:
+        assert torch.equal(s, ref_s) and torch.equal(v, ref_v)
+    else:
+        for b, (n_p, ng, box) in enumerate(BOXES):
+            sb, rb = ens.split(s)[b], ens.split(ref_s)[b]
+            vb, rvb = ens.split(v)[b], ens.split(ref_v)[b]
+            assert float((sb - rb).abs().max()) <= 1e-4 * box / ng, b
+            assert float((vb - rvb).abs().max()) <= 1e-4 * float(rvb.pow(2).mean().sqrt()), b
 
 
 def test_graph_replay_equals_direct_launches(cola, ens):
-    ens.tuning = (256, 0, 0)
+    ens.tuning = (256, 0, 0, 0)
     ens.use_graphs(True)
     s_g, v_g = run_steps(ens, SEEDS, 3)
     s_g2, v_g2 = run_steps(ens, SEEDS, 3)  # second pass replays the recorded graphs
@@ -120,9 +131,9 @@ def test_graph_replay_launches_eleven_kernels_per_step(cola, ens):
 def test_autotuner_picks_the_fastest_candidate(cola, ens):
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     best, ms = ens.tune(s, reps=2)
-    assert (best.threads, best.tile_shape, best.blocks_per_sm) == ens.tuning
-    assert np.all(ms > 0) and len(ms) == 8
-    order = [(t, sh, b) for t in (128, 256) for sh in (0, 1) for b in (0, 2)]
+    assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix) == ens.tuning
+    assert np.all(ms > 0) and len(ms) == 16
+    order = [(t, sh, b, r) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
     assert order[int(np.argmin(ms))] == ens.tuning
     ens.status()
 
