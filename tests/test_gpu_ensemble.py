@@ -6,7 +6,8 @@ code as the single-box kernels, only grouped differently into blocks and launche
 deposit sums are integers (order-independent).  So each box's result must equal the
 single-box result bit for bit -- and the single-box path is the one checked against the
 float64 oracle in test_gpu_parity.py.  The same holds for every launch shape the autotuner
-may pick and for graph replay versus direct launches.
+may pick with the single-box FFT factorisation (radix variant 0) and for graph replay versus
+direct launches; the second factorisation (variant 1) agrees to float32 rounding.
 """
 import numpy as np
 import pytest
