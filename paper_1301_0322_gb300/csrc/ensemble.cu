@@ -335,6 +335,12 @@ struct cola_ensemble {
   // graphs
   bool use_graphs = true;
   cudaStream_t cap = nullptr;
+  // per-box work outside the step (noise, initial conditions, density, P(k)) runs on kForks
+  // side streams forked from and joined back into the caller's (or the capture) stream
+  static constexpr int kForks = 8;
+  cudaStream_t side[kForks] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kForks] = {};
   struct Cached {
     cudaGraphExec_t exec = nullptr;
     std::vector<uintptr_t> key;  // pointers and scalars the recorded launches baked in
@@ -348,6 +354,11 @@ struct cola_ensemble {
     for (auto& c : graphs)
       if (c.exec) cudaGraphExecDestroy(c.exec);
     if (cap) cudaStreamDestroy(cap);
+    for (int k = 0; k < kForks; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (join_ev[k]) cudaEventDestroy(join_ev[k]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
     for (auto* p : plans) cola_plan_destroy(p);
   }
 };
@@ -583,6 +594,24 @@ int replay(cola_ensemble* e, cola_ensemble::Cached& c, const std::vector<uintptr
 
 uintptr_t u(const void* p) { return reinterpret_cast<uintptr_t>(p); }
 
+// Run per_box(b, stream) for every box with the boxes spread over the side streams, forked from
+// and joined back into `st` (inside a capture the forks become parallel graph branches; the
+// boxes use disjoint workspaces, so their work is independent).
+template <class F>
+int fork_join(cola_ensemble* e, cudaStream_t st, F&& per_box) {
+  constexpr int K = cola_ensemble::kForks;
+  COLA_CUDA_CHECK(cudaEventRecord(e->fork_ev, st));
+  for (int k = 0; k < K; ++k) COLA_CUDA_CHECK(cudaStreamWaitEvent(e->side[k], e->fork_ev, 0));
+  int rc = COLA_OK;
+  for (int b = 0; b < e->nbox && !rc; ++b) rc = per_box(b, e->side[b % K]);
+  for (int k = 0; k < K; ++k) {  // join even after a failure: no stream may stay forked
+    const cudaError_t r1 = cudaEventRecord(e->join_ev[k], e->side[k]);
+    const cudaError_t r2 = cudaStreamWaitEvent(st, e->join_ev[k], 0);
+    if (!rc && (r1 != cudaSuccess || r2 != cudaSuccess)) rc = fail(COLA_ECUDA, "ensemble stream join failed");
+  }
+  return rc;
+}
+
 }  // namespace
 }  // namespace cola
 
@@ -696,6 +725,13 @@ int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes,
   COLA_CUDA_CHECK(cudaGetDevice(&dev));
   COLA_CUDA_CHECK(cudaDeviceGetAttribute(&ens->num_sms, cudaDevAttrMultiProcessorCount, dev));
   if (!ens->cap) COLA_CUDA_CHECK(cudaStreamCreateWithFlags(&ens->cap, cudaStreamNonBlocking));
+  if (!ens->fork_ev) {
+    COLA_CUDA_CHECK(cudaEventCreateWithFlags(&ens->fork_ev, cudaEventDisableTiming));
+    for (int k = 0; k < cola_ensemble::kForks; ++k) {
+      COLA_CUDA_CHECK(cudaStreamCreateWithFlags(&ens->side[k], cudaStreamNonBlocking));
+      COLA_CUDA_CHECK(cudaEventCreateWithFlags(&ens->join_ev[k], cudaEventDisableTiming));
+    }
+  }
   ens->ws_base = dev_ptr;
   return configure(ens, st);
 }
@@ -714,11 +750,9 @@ int cola_ensemble_noise(cola_ensemble* ens, const uint64_t* seeds, float* noise,
   std::vector<uintptr_t> key{u(noise)};
   for (int b = 0; b < ens->nbox; ++b) key.push_back((uintptr_t)seeds[b]);
   return replay(ens, ens->graphs[ens->nsteps + 1], key, [&](cudaStream_t st) {
-    for (int b = 0; b < ens->nbox; ++b) {
-      const int r = cola_noise(ens->plans[b], seeds[b], noise + ens->poff[b], (cola_stream)st);
-      if (r) return r;
-    }
-    return (int)COLA_OK;
+    return fork_join(ens, st, [&](int b, cudaStream_t sb) {
+      return cola_noise(ens->plans[b], seeds[b], noise + ens->poff[b], (cola_stream)sb);
+    });
   }, (cudaStream_t)stream);
 }
 
@@ -728,12 +762,10 @@ int cola_ensemble_ic_2lpt(cola_ensemble* ens, const float* noise, float* s, floa
   if (rc) return rc;
   if (!noise || !s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
   return replay(ens, ens->graphs[ens->nsteps + 2], {u(noise), u(s), u(v), u(s1), u(s2)}, [&](cudaStream_t st) {
-    for (int b = 0; b < ens->nbox; ++b) {
+    return fork_join(ens, st, [&](int b, cudaStream_t sb) {
       const int64_t o = ens->poff[b], o3 = 3 * ens->poff[b];
-      const int r = cola_ic_2lpt(ens->plans[b], noise + o, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)st);
-      if (r) return r;
-    }
-    return (int)COLA_OK;
+      return cola_ic_2lpt(ens->plans[b], noise + o, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)sb);
+    });
   }, (cudaStream_t)stream);
 }
 
@@ -753,11 +785,9 @@ int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola
   if (rc) return rc;
   if (!s || !delta) return fail(COLA_EINVAL, "null array");
   return replay(ens, ens->graphs[ens->nsteps + 3], {u(s), u(delta)}, [&](cudaStream_t st) {
-    for (int b = 0; b < ens->nbox; ++b) {
-      const int r = cola_density(ens->plans[b], s + 3 * ens->poff[b], nullptr, delta + ens->moff[b], (cola_stream)st);
-      if (r) return r;
-    }
-    return (int)COLA_OK;
+    return fork_join(ens, st, [&](int b, cudaStream_t sb) {
+      return cola_density(ens->plans[b], s + 3 * ens->poff[b], nullptr, delta + ens->moff[b], (cola_stream)sb);
+    });
   }, (cudaStream_t)stream);
 }
 
@@ -769,13 +799,11 @@ int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, d
   if (nbins < 1 || nbins > ens->min_ng) return fail(COLA_EINVAL, "nbins must be in [1, smallest ng]");
   return replay(ens, ens->graphs[ens->nsteps + 4], {u(delta), (uintptr_t)nbins, u(k), u(pk), u(nmodes)},
                 [&](cudaStream_t st) {
-                  for (int b = 0; b < ens->nbox; ++b) {
+                  return fork_join(ens, st, [&](int b, cudaStream_t sb) {
                     const size_t o = (size_t)b * nbins;
-                    const int r = cola_power(ens->plans[b], delta + ens->moff[b], nbins, k + o, pk + o, nmodes + o,
-                                             (cola_stream)st);
-                    if (r) return r;
-                  }
-                  return (int)COLA_OK;
+                    return cola_power(ens->plans[b], delta + ens->moff[b], nbins, k + o, pk + o, nmodes + o,
+                                      (cola_stream)sb);
+                  });
                 },
                 (cudaStream_t)stream);
 }
