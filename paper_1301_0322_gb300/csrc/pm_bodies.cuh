@@ -204,7 +204,7 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
           const float wk = sx2[c] * wy * sz2[n];
           den *= deconv == 2 ? wk * wk : wk;
         }
-        gk = norm / den;
+        gk = __fdividef(norm, den);  // fast reciprocal: <= 2 ulp, far below the transforms' rounding
       }
       S0[i] = c_scale(S0[i], gk);
     }
