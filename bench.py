@@ -141,7 +141,7 @@ def algorithmic_bytes(name, n_p, ng):
     if name.startswith("fft_x_r2c") or name.startswith("fft_x_c2r_"):
         return H + n**3 * 4                # real rows <-> half-spectrum rows
     if name.startswith("deposit_fftx"):
-        return 16 * np3 + H                # index + displacement per particle, half spectrum out
+        return 12 * np3 + H                # fixed-point coordinates per particle, half spectrum out
     if name.startswith("fft_z_green"):
         return H + 2 * H                   # delta_k in; B and Gz out
     if name.startswith("fft_y_inv3"):
@@ -155,7 +155,7 @@ def algorithmic_bytes(name, n_p, ng):
         "kspace_force": 4 * 8 * ng * ng * (ng // 2 + 1),
         "gather_kick_drift": 72 * np3 + 12 * ng3,  # s, v, s1, s2 in, s, v out; 3 force meshes once
         "keys": 16 * np3,
-        "scatter": 8 * np3,
+        "scatter": 32 * np3,               # key + displacement in; index + fixed-point coordinates out
         "power_bin": 8 * ng * ng * (ng // 2 + 1),
     }
     return table.get(name)
