@@ -46,7 +46,8 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
 
 // ---- 1. deposit + x r2c -----------------------------------------------------------------------
 // block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
-// bytes of shared memory; ints: 28 ints of shared memory
+// bytes of shared memory (the cells' low 32-bit words, then their high words; afterwards the
+// rows' transform buffers); ints: 28 ints of shared memory
 // coords: [3][cstride] fixed-point CIC coordinates in bin order (offsets index them directly)
 template <int N, int TY, int TZ, class CM = FFTConf<N / 2>>
 __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl,
@@ -86,6 +87,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   __syncthreads();
   const int total = rpre[9];
   const unsigned long long one = 1ull << g.fbits;
+  unsigned* lo = reinterpret_cast<unsigned*>(acc);
+  unsigned* hi = lo + ROWS * N;
   constexpr int U = 4;  // particles in flight per thread
   const uint32_t fmask = (uint32_t)one - 1u;
   for (int base = threadIdx.x; base < total; base += NT * U) {
@@ -123,22 +126,27 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
           const int ly = (dy ? wrap_inc(cy, N) : cy) - y0;
           if (ly < 0 || ly >= TY) continue;
           const unsigned long long wzy = wz * (dy ? (unsigned long long)ty : one - ty);
-          unsigned long long* row = acc + (lz * TY + ly) * N;
-          atomicAdd(row + cx, wzy * wx0);
-          atomicAdd(row + cx1, wzy * wx1);
+          const int row = (lz * TY + ly) * N;
+          acc_add64(lo, hi, row + cx, wzy * wx0);
+          acc_add64(lo, hi, row + cx1, wzy * wx1);
         }
       }
     }
   }
   __syncthreads();
-  // real-to-complex FFT of each tile row; z[n] = (delta[2n], delta[2n+1])
+  // real-to-complex FFT of each tile row; z[n] = (delta[2n], delta[2n+1]).  The transform
+  // buffers overlay the accumulators: fft_1d reads all its inputs before a block barrier
+  // that precedes its first shared-memory write.
   const int t = threadIdx.x % T, w = threadIdx.x / T;
-  const unsigned long long* arow = acc + w * N;
+  const uint2* lrow = reinterpret_cast<const uint2*>(lo + w * N);
+  const uint2* hrow = reinterpret_cast<const uint2*>(hi + w * N);
   float2* buf = reinterpret_cast<float2*>(acc) + w * LD;
   bool overflow = false;
   auto load = [&](int n) -> float2 {
-    const unsigned long long a = arow[2 * n], b = arow[2 * n + 1];
-    overflow |= ((a | b) >> 62) != 0ull;
+    const uint2 l = lrow[n], h = hrow[n];
+    overflow |= ((h.x | h.y) >> 30) != 0u;
+    const unsigned long long a = ((unsigned long long)h.x << 32) | l.x;
+    const unsigned long long b = ((unsigned long long)h.y << 32) | l.y;
     return make_float2(fmaf(__ull2float_rn(a), dscale, -1.0f), fmaf(__ull2float_rn(b), dscale, -1.0f));
   };
   auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };

@@ -43,4 +43,20 @@ __device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, in
 
 __device__ __forceinline__ int wrap_inc(int c, int n) { return c + 1 == n ? 0 : c + 1; }
 
+// Exact 64-bit accumulation in shared memory held as two 32-bit words per cell, the low words
+// in one array and the high words in another: the low word is added with carry detection (the
+// atomic returns the previous value; the add wrapped iff the new value is below it) and the
+// high word receives the upper half plus that carry.  lo[i] + 2^32 hi[i] is the 64-bit sum
+// modulo 2^64, whatever the order of the adds.  Two 32-bit shared atomics run at about twice
+// the rate of one 64-bit shared atomic on sm_103a.
+__device__ __forceinline__ void acc_add64(unsigned* lo, unsigned* hi, int i, unsigned long long w) {
+  const unsigned l = (unsigned)w, h = (unsigned)(w >> 32);
+  const unsigned old = atomicAdd(lo + i, l);
+  const unsigned up = h + ((old + l < old) ? 1u : 0u);
+  if (up) atomicAdd(hi + i, up);
+}
+__device__ __forceinline__ unsigned long long acc_value(const unsigned* lo, const unsigned* hi, int i) {
+  return ((unsigned long long)hi[i] << 32) | lo[i];
+}
+
 }  // namespace cola

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const flo
   __syncthreads();
   const int total = rpre[9];
   const unsigned long long one = 1ull << g.fbits;
+  unsigned* lo = reinterpret_cast<unsigned*>(acc);
+  unsigned* hi = lo + ncell;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
     int r = 0;
 #pragma unroll
@@ -148,9 +150,9 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const flo
         const int ly = y - y0;
         if (ly < 0 || ly >= TY) continue;
         const unsigned long long wzy = wz * (dy ? (unsigned long long)ty : one - ty);
-        unsigned long long* row = acc + (lz * TY + ly) * ng;
-        atomicAdd(row + cx, wzy * wx0);
-        atomicAdd(row + cx1, wzy * wx1);
+        const int row = (lz * TY + ly) * ng;
+        acc_add64(lo, hi, row + cx, wzy * wx0);
+        acc_add64(lo, hi, row + cx1, wzy * wx1);
       }
     }
   }
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const flo
     const int lz = i / (TY * ng), rem = i - lz * (TY * ng);
     const int ly = rem / ng, x = rem - ly * ng;
     const int64_t gi = ((int64_t)(z0 + lz) * ng + (y0 + ly)) * ng + x;
-    const unsigned long long v = acc[i];
+    const unsigned long long v = acc_value(lo, hi, i);
     overflow |= (v >> 62) != 0ull;
     if (rho) rho[gi] = (int64_t)v;
     if (delta) delta[gi] = fmaf(__ull2float_rn(v), dscale, -1.0f);
