@@ -103,6 +103,11 @@ def test_deposit_bit_exact(cola, case):
     d = host(delta).reshape(ng, ng, ng)
     dref = ref.astype(np.float64) * (ng**3 / (n_p**3 * 2.0**48)) - 1.0
     assert np.abs(d - dref).max() <= 1e-6 * (1.0 + np.abs(dref).max())
+    # exactly fma(float32(rho), dscale, -1): the integer rounded to the nearest float32 (ties to
+    # even), times dscale = (ng/np)^3 2^-48 (a float32 without rounding), minus 1 with one rounding
+    # (the float64 product is exact; the float64 subtraction is exact unless rho is tiny)
+    d32 = (ref.astype(np.float32).astype(np.float64) * (ng**3 / (n_p**3 * 2.0**48)) - 1.0).astype(np.float32)
+    assert np.array_equal(d, d32)
     plan.status()
 
 
