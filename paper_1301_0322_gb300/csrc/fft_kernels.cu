@@ -49,13 +49,15 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
   fft_1d<M, 2, false>(t, tw, load, mem, store);
   __syncthreads();
   float2* dst = out + row * P;
-  for (int k = t; k <= M; k += T) {
-    const float2 a = buf[xpad(k == M ? 0 : k)];
+  // X[k] = e + p and X[M - k] = conj(e - p) from one pair Z[k], Z[M - k] (p = W^k (-i d))
+  for (int k = t; k <= M / 2; k += T) {
+    const float2 a = buf[xpad(k)];
     const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
     const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
     const float2 d = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
-    const float2 o = make_float2(d.y, -d.x);  // -i d
-    dst[k] = c_add(e, c_mul(__ldg(tw + k), o));
+    const float2 p = c_mul(__ldg(tw + k), make_float2(d.y, -d.x));
+    dst[k] = c_add(e, p);
+    if (2 * k != M) dst[M - k] = c_conj(c_sub(e, p));
   }
 }
 

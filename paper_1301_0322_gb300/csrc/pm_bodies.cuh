@@ -156,12 +156,17 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   __syncthreads();
   const int lz = w / TY, ly = w - lz * TY;
   float2* dst = out + ((int64_t)(z0 + lz) * N + (y0 + ly)) * P;
-  for (int k = t; k <= M; k += T) {
-    const float2 a = buf[xpad(k == M ? 0 : k)];
+  // X[k] and X[M - k] from one pair Z[k], Z[M - k]: with e = (Z[k] + conj Z[M - k]) / 2,
+  // d = (Z[k] - conj Z[M - k]) / 2 and p = W^k (-i d), X[k] = e + p and X[M - k] = conj(e - p)
+  // (as W^(M - k) = -conj W^k); k = 0 gives X[0] and X[M] from Z[0]
+  for (int k = t; k <= M / 2; k += T) {
+    const float2 a = buf[xpad(k)];
     const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
     const float2 e = c_scale(c_add(a, b), 0.5f);
     const float2 d = c_scale(c_sub(a, b), 0.5f);
-    dst[k] = c_add(e, c_mul(__ldg(tw + k), make_float2(d.y, -d.x)));
+    const float2 p = c_mul(__ldg(tw + k), make_float2(d.y, -d.x));
+    dst[k] = c_add(e, p);
+    if (2 * k != M) dst[M - k] = c_conj(c_sub(e, p));
   }
 }
 
