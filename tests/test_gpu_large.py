@@ -1,15 +1,18 @@
-"""Parity at the large single-box size: 1024^3 particles on a 2048^3 mesh, L = 1000 Mpc/h.
+"""Parity at the full single-box sizes: 256^3 particles on a 768^3 mesh (L = 100 Mpc/h, the
+benchmark workload, in the launch configuration the benchmark times) and 1024^3 particles on a
+2048^3 mesh (L = 1000 Mpc/h).
 
-The three-dimensional oracle cannot run at this size (one float64 mesh is 69 GB), so the
-force is checked on inputs whose PM force the oracle computes exactly in one dimension: a
-lattice displaced by a plane wave along one axis (oracle.mesh.unit_force_axis_wave, pinned
-against the brute 3-D force in test_oracle_mesh.py).  One force evaluation per axis runs every
-fused pass at N = 2048 (deposit + x r2c, forward y, z with the Green's function, the inverse y
-and x passes) and the gather, with the transform axis of the wave different each time.
-Tolerance as the small-size force parity: 3e-4 of max |g| (positions quantised to 2^-16 cell,
-float32 transforms); the transverse components vanish up to float32 rounding.
+The three-dimensional oracle cannot run at these sizes (one float64 mesh is 3.6 GB at 768^3 and
+69 GB at 2048^3, and its transforms take minutes), so the force is checked on inputs whose PM
+force the oracle computes exactly in one dimension: a lattice displaced by a plane wave along
+one axis (oracle.mesh.unit_force_axis_wave, pinned against the brute 3-D force in
+test_oracle_mesh.py).  One force evaluation per axis runs every fused pass (deposit + x r2c,
+forward y, z with the Green's function, the inverse y and x passes) and the gather, with the
+transform axis of the wave different each time.  Tolerance as the small-size force parity:
+3e-4 of max |g| (positions quantised to 2^-16 cell, float32 transforms); the transverse
+components vanish up to float32 rounding.
 
-A full COLA step at this size (2LPT from Philox seed 3, first kick + drift) then checks the
+A full COLA step at each size (2LPT from Philox seed 3, first kick + drift) then checks the
 error flags, finiteness and momentum conservation.
 """
 import numpy as np
@@ -20,8 +23,8 @@ from oracle import mesh as omesh
 
 pytestmark = pytest.mark.gpu
 
-N_P, NG, BOX = 1024, 2048, 1000.0
-NEEDED_BYTES = 250 * 10**9  # workspace 215 GB + displacement and force arrays 26 GB
+# (particles per side, mesh, box in Mpc/h, device bytes needed: workspace + particle arrays)
+SIZES = {768: (256, 768, 100.0, 16 * 10**9), 2048: (1024, 2048, 1000.0, 250 * 10**9)}
 
 
 @pytest.fixture(scope="module")
@@ -33,20 +36,22 @@ def cola():
     return c
 
 
-@pytest.fixture(scope="module")
-def big_plan(cola):
+@pytest.fixture(scope="module", params=sorted(SIZES))
+def big_plan(cola, request):
+    n_p, ng, box, needed = SIZES[request.param]
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
-    if free < NEEDED_BYTES:
-        pytest.skip(f"needs {NEEDED_BYTES / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
-    plan = cola.Plan(np_side=N_P, ng=NG, box=BOX)
-    yield plan
+    if free < needed:
+        pytest.skip(f"needs {needed / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box)
+    yield plan, n_p, ng, box
     del plan
     torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("axis,m", [(0, 1), (1, 2), (2, 5)])
-def test_plane_wave_force_at_2048(big_plan, axis, m):
+def test_plane_wave_force_at_full_size(big_plan, axis, m):
+    big_plan, N_P, NG, BOX = big_plan
     k = 2 * np.pi * m / BOX
     line = (0.4 / k * np.sin(k * np.arange(N_P) * BOX / N_P)).astype(np.float32)
     shape = [1, 1, 1]
@@ -67,15 +72,17 @@ def test_plane_wave_force_at_2048(big_plan, axis, m):
         err = max(err, float((chunk[axis] - refc).abs().max()))
         others = [c for c in range(3) if c != axis]
         trans = max(trans, float(chunk[others].abs().max()))
-    print(f"axis {axis}, mode {m}: max |g - g_oracle| / max |g| = {err / scale:.2e}, transverse {trans / scale:.2e}")
+    print(f"N = {NG}, axis {axis}, mode {m}: max |g - g_oracle| / max |g| = {err / scale:.2e}, "
+          f"transverse {trans / scale:.2e}")
     assert err <= 3e-4 * scale
     assert trans <= 1e-4 * scale
 
 
-def test_full_step_at_2048_conserves_momentum(cola, big_plan):
+def test_full_step_at_full_size_conserves_momentum(cola, big_plan):
     # 2LPT initial conditions from Philox seed 3, then the first kick + drift: the PM force
     # sums to zero over the particles (antisymmetric operator, same deposit and gather
     # weights) and s1, s2 have zero mean, so the kicked velocities sum to ~0
+    big_plan = big_plan[0]
     noise = big_plan.noise(3)
     s, v, s1, s2 = big_plan.ic_2lpt(noise)
     del noise
