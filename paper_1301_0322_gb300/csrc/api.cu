@@ -339,7 +339,7 @@ int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta
   if (!s || (!rho_fix && !delta)) return fail(COLA_EINVAL, "null array");
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = bin_particles(plan, s, st))) return rc;
-  return launch_deposit(plan->geo, plan->tiles, s, plan->ws.idx, plan->ws.offsets, rho_fix, delta, plan->ws.err, st);
+  return launch_deposit(plan->geo, plan->tiles, plan->ws.coords, plan->ws.offsets, rho_fix, delta, plan->ws.err, st);
 }
 
 int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, double* pk, int64_t* nmodes,

@@ -123,8 +123,8 @@ int scan_block_count(const Tiles& t);
 int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* block_sums, cudaStream_t st);
 int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, unsigned* idx, uint32_t* coords,
                    cudaStream_t st);
-int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
-                   int64_t* rho, float* delta, int* err, cudaStream_t st);
+int launch_deposit(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+                   float* delta, int* err, cudaStream_t st);
 int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
                         cudaStream_t st);
 // the fused mesh passes of one force evaluation (pm_fft_kernels.cu): deposit + x r2c, y pass,

@@ -90,14 +90,14 @@ __global__ void k_scatter(Geometry g, const float* __restrict__ s, const int* __
 }
 
 // ---- deposit ----------------------------------------------------------------------------------
-// One block per tile of TY x TZ mesh rows (whole x extent).  It reads the particles binned to
-// the tile and the boundary regions of its three lower neighbours, accumulates exact int64
-// CIC weights in shared memory and writes the rows once (int64 and/or float overdensity).
+// One block per tile of TY x TZ mesh rows (whole x extent).  It reads the fixed-point CIC
+// coordinates (stored by the scatter in bin order) of the particles binned to the tile and to
+// the boundary regions of its three lower neighbours, accumulates exact int64 CIC weights in
+// shared memory and writes the rows once (int64 and/or float overdensity).
 template <int TY, int TZ>
-__global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const float* __restrict__ s,
-                                                 const unsigned* __restrict__ idx, const int* __restrict__ offsets,
-                                                 int64_t* __restrict__ rho, float* __restrict__ delta,
-                                                 float dscale, int* __restrict__ err) {
+__global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uint32_t* __restrict__ coords,
+                                                 const int* __restrict__ offsets, int64_t* __restrict__ rho,
+                                                 float* __restrict__ delta, float dscale, int* __restrict__ err) {
   extern __shared__ unsigned long long acc[];
   __shared__ int rbeg[9], rpre[10];
   const int ng = g.ng;
@@ -129,13 +129,12 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const flo
     int r = 0;
 #pragma unroll
     for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
-    const int64_t p = idx[rbeg[r] + (i - rpre[r])];
-    int ix, iy, iz;
-    lattice_index(g, p, ix, iy, iz);
-    int cx, tx, cy, ty, cz, tz;
-    fixed_axis(g, ix, s[p], cx, tx);
-    fixed_axis(g, iy, s[g.np3 + p], cy, ty);
-    fixed_axis(g, iz, s[2 * g.np3 + p], cz, tz);
+    const int64_t pos = rbeg[r] + (i - rpre[r]);
+    const uint32_t fmask = (uint32_t)one - 1u;
+    const uint32_t fx = __ldg(coords + pos), fy = __ldg(coords + g.np3 + pos), fz = __ldg(coords + 2 * g.np3 + pos);
+    const int cx = (int)(fx >> g.fbits), tx = (int)(fx & fmask);
+    const int cy = (int)(fy >> g.fbits), ty = (int)(fy & fmask);
+    const int cz = (int)(fz >> g.fbits), tz = (int)(fz & fmask);
     const int cx1 = wrap_inc(cx, ng);
     const unsigned long long wx0 = one - tx, wx1 = tx;
 #pragma unroll
@@ -264,8 +263,8 @@ int launch_scatter(const Geometry& g, const float* s, const int* keys, int* curs
 }
 
 template <int TY, int TZ>
-static int deposit_t(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
-                     int64_t* rho, float* delta, int* err, cudaStream_t st) {
+static int deposit_t(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+                     float* delta, int* err, cudaStream_t st) {
   const size_t smem = (size_t)TY * TZ * g.ng * sizeof(unsigned long long);
   if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "deposit tile does not fit in shared memory");
   if (smem > 32 * 1024)
@@ -273,16 +272,16 @@ static int deposit_t(const Geometry& g, const Tiles& t, const float* s, const un
   const double ng3 = (double)g.ng * g.ng * g.ng;
   const float dscale = (float)(ng3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
   { LaunchScope ls_(TY == 2 ? "deposit_2x2" : (TZ == 2 ? "deposit_4x2" : "deposit_4x4"), st);
-  k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, s, idx, offsets, rho, delta, dscale, err); }
+  k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, coords, offsets, rho, delta, dscale, err); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 
-int launch_deposit(const Geometry& g, const Tiles& t, const float* s, const unsigned* idx, const int* offsets,
-                   int64_t* rho, float* delta, int* err, cudaStream_t st) {
-  if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, s, idx, offsets, rho, delta, err, st);
-  if (t.ty == 4 && t.tz == 2) return deposit_t<4, 2>(g, t, s, idx, offsets, rho, delta, err, st);
-  if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, s, idx, offsets, rho, delta, err, st);
+int launch_deposit(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+                   float* delta, int* err, cudaStream_t st) {
+  if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, coords, offsets, rho, delta, err, st);
+  if (t.ty == 4 && t.tz == 2) return deposit_t<4, 2>(g, t, coords, offsets, rho, delta, err, st);
+  if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, coords, offsets, rho, delta, err, st);
   return fail(COLA_EUNSUPPORTED, "deposit: unsupported tile shape");
 }
 

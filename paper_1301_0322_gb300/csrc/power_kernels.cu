@@ -35,7 +35,13 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
   extern __shared__ double pacc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nh = ng / 2 + 1;
+  // 1 / W_x^2 = sinc^-4 of every k_x, once per block (after the accumulators)
+  float* inv_wx2 = reinterpret_cast<float*>(pacc + (size_t)nwarps * nbins * NQ);
   for (int i = threadIdx.x; i < nwarps * nbins * NQ; i += blockDim.x) pacc[i] = 0.0;
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    const float sx = sinc_pi_p(i, ng), wx = sx * sx;
+    inv_wx2[i] = 1.0f / (wx * wx);
+  }
   __syncthreads();
   double* mine = pacc + (size_t)warp * nbins * NQ;
   const int64_t nrows = (int64_t)ng * ng;
@@ -45,6 +51,7 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
     const int myz = ny * ny + nz * nz;
     const float sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
     const float wyz = (sy * sy) * (sz * sz);
+    const float row_scale = pnorm / (wyz * wyz);
     const float2* rowp = dk + row * P;
     const float2* rowq = NF == 2 ? dk2 + row * P : nullptr;
     for (int c0 = 0; c0 < nh; c0 += 32) {
@@ -60,9 +67,7 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
           b = sb - 1;
           const float w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
           const float2 d = rowp[kx];
-          const float sx = sinc_pi_p(kx, ng);
-          const float win = (sx * sx) * wyz;
-          const float scale = w * pnorm / (win * win);
+          const float scale = w * (row_scale * inv_wx2[kx]);  // w P-normalisation / W(k)^2
           q[0] = w * kf * sqrtf((float)m);
           q[1] = (d.x * d.x + d.y * d.y) * scale;
           if constexpr (NF == 2) {
@@ -166,7 +171,7 @@ static int power_bin_t(int ng, int P, double box, int nbins, const float2* dk, c
   const double ng6 = std::pow((double)ng, 6.0);
   const float pnorm = (float)(box * box * box / ng6);
   const int warps = power_warps(nbins, NQ);
-  const size_t smem = (size_t)warps * nbins * NQ * sizeof(double);
+  const size_t smem = (size_t)warps * nbins * NQ * sizeof(double) + sizeof(float) * (ng / 2 + 1);
   if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "power spectrum: too many bins for shared memory");
   if (smem > 32 * 1024)
     COLA_CUDA_CHECK(cudaFuncSetAttribute(k_power_bin<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
