@@ -188,6 +188,7 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   p->tiles.nbins = p->tiles.nty * p->tiles.ntz * 4;
   p->Pg = padded_half((int)c.ng);
   p->Pp = padded_half((int)c.np);
+  p->binned_gather = (double)sizeof(float2) * c.ng * c.ng * p->Pg >= (double)sizeof(float) * p->geo.np3;
   std::string why;
   int rc = build_coefficients(c, p->coef64, p->pk_amp, p->d2u1, why);
   if (rc) {
@@ -317,8 +318,15 @@ int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = force_meshes(plan, s, st))) return rc;
   const int mode = step == plan->cfg.nsteps ? 1 : 0;
-  return launch_gather_kick_drift(plan->geo, plan->ws.freal, s, v, s1, s2, plan->ws.coef + (size_t)step * kCoef32,
-                                  mode, nullptr, st);
+  const float* coef = plan->ws.coef + (size_t)step * kCoef32;
+  const Workspace& w = plan->ws;
+  if (!plan->binned_gather)
+    return launch_gather_kick_drift(plan->geo, w.freal, s, v, s1, s2, coef, mode, nullptr, st);
+  // the gathered forces go to the half-spectrum buffers, free once the force meshes exist
+  float* f[3] = {reinterpret_cast<float*>(w.meshA), reinterpret_cast<float*>(w.meshG[1]),
+                 reinterpret_cast<float*>(w.meshG[2])};
+  if ((rc = launch_gather_binned(plan->geo, w.freal, w.idx, w.coords, f[0], f[1], f[2], st))) return rc;
+  return launch_kick_drift(plan->geo, f[0], f[1], f[2], s, v, s1, s2, coef, mode, st);
 }
 
 int cola_force(cola_plan* plan, const float* s, float* g, cola_stream stream) {
@@ -328,8 +336,8 @@ int cola_force(cola_plan* plan, const float* s, float* g, cola_stream stream) {
   if (!s || !g) return fail(COLA_EINVAL, "null array");
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = force_meshes(plan, s, st))) return rc;
-  return launch_gather_kick_drift(plan->geo, plan->ws.freal, const_cast<float*>(s), nullptr, nullptr, nullptr,
-                                  plan->ws.coef, 2, g, st);
+  const int64_t n3 = plan->geo.np3;
+  return launch_gather_binned(plan->geo, plan->ws.freal, plan->ws.idx, plan->ws.coords, g, g + n3, g + 2 * n3, st);
 }
 
 int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta, cola_stream stream) {

@@ -80,6 +80,8 @@ struct cola_plan {
   cola::Tiles tiles;
   int Pg = 0, Pp = 0;  // padded half-spectrum row lengths (complex) for ng and np
   int64_t ng3 = 0;
+  // the step gathers in bin order into the half-spectrum buffers (each holds np^3 floats)
+  bool binned_gather = false;
   std::vector<double> coef64;
   std::vector<float> coef32;
   std::vector<float2> tw_g, tw_p;
@@ -135,6 +137,12 @@ int launch_force_passes(const Geometry& g, const Tiles& tl, const uint32_t* coor
 // mode 0: kick + drift, 1: kick + L+ (last force evaluation), 2: write the gathered unit force to gout
 int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, float* v, const float* s1,
                              const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st);
+// the gather in bin order of the last binning (idx, coords) into fj[p], and the kick/drift in
+// lattice order from those forces
+int launch_gather_binned(const Geometry& g, const float* fmesh, const unsigned* idx, const uint32_t* coords,
+                         float* f0, float* f1, float* f2, cudaStream_t st);
+int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,
+                      const float* s1, const float* s2, const float* coef_row, int mode, cudaStream_t st);
 
 // IC kernels (ic_kernels.cu)
 int launch_noise(int np, uint64_t seed, float* out, cudaStream_t st);

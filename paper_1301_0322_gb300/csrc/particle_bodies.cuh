@@ -69,24 +69,12 @@ __device__ __forceinline__ void scatter_body(const Geometry& g, const float* __r
   }
 }
 
-// CIC gather of the three force meshes fmesh [3][ng^3] at particle p (the deposit's weights),
-// then (mode 0) Kick + Drift of eq. KDKALC, (mode 1) the final Kick + L+ of eq. Lops, or
-// (mode 2) the gathered force alone into gout [3][np^3].
-__device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const float* __restrict__ fmesh,
-                                                       float* __restrict__ s, float* __restrict__ v,
-                                                       const float* __restrict__ s1, const float* __restrict__ s2,
-                                                       const float* __restrict__ coef, int mode,
-                                                       float* __restrict__ gout, int64_t p) {
-  const int64_t n3 = g.np3;
+// CIC gather of the three force meshes fmesh [3][ng^3] for a cloud that starts at cells c with
+// upper-neighbour weights t / 2^F (the deposit's weights).
+__device__ __forceinline__ void gather_force(const Geometry& g, const float* __restrict__ fmesh, const int (&c)[3],
+                                             const int (&t)[3], float (&f)[3]) {
   const int ng = g.ng;
   const int64_t ng3 = (int64_t)ng * ng * ng;
-  int ix, iy, iz;
-  lattice_index(g, p, ix, iy, iz);
-  const float sp[3] = {s[p], s[n3 + p], s[2 * n3 + p]};
-  int c[3], t[3];
-  fixed_axis(g, ix, sp[0], c[0], t[0]);
-  fixed_axis(g, iy, sp[1], c[1], t[1]);
-  fixed_axis(g, iz, sp[2], c[2], t[2]);
   const float inv_one = 1.0f / (float)(1 << g.fbits);
   float w1[3], w0[3];
 #pragma unroll
@@ -97,7 +85,7 @@ __device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const 
   const int xs[2] = {c[0], wrap_inc(c[0], ng)};
   const int ys[2] = {c[1], wrap_inc(c[1], ng)};
   const int zs[2] = {c[2], wrap_inc(c[2], ng)};
-  float f[3] = {0.f, 0.f, 0.f};
+  f[0] = f[1] = f[2] = 0.f;
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -112,11 +100,15 @@ __device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const 
         for (int j = 0; j < 3; ++j) f[j] = fmaf(w, __ldg(fmesh + j * ng3 + gi), f[j]);
       }
     }
-  if (mode == 2) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gout[j * n3 + p] = f[j];
-    return;
-  }
+}
+
+// With the gathered force f of particle p: (mode 0) Kick + Drift of eq. KDKALC, (mode 1) the
+// final Kick + L+ of eq. Lops.
+__device__ __forceinline__ void kick_drift_update(const Geometry& g, float* __restrict__ s, float* __restrict__ v,
+                                                  const float* __restrict__ s1, const float* __restrict__ s2,
+                                                  const float* __restrict__ coef, int mode, int64_t p,
+                                                  const float (&f)[3]) {
+  const int64_t n3 = g.np3;
   // explicit FMA chains: the same rounding in every kernel this body is inlined into
   const float cKF = __ldg(coef + kCKF), cK1 = __ldg(coef + kCK1), cK2 = __ldg(coef + kCK2);
 #pragma unroll
@@ -126,12 +118,35 @@ __device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const 
     vj = __fadd_rn(vj, fmaf(cKF, f[j], fmaf(-cK1, a1, __fmul_rn(-cK2, a2))));  // Kick (eq. KDKALC)
     if (mode == 0) {
       const float dj = fmaf(__ldg(coef + kCD), vj, fmaf(__ldg(coef + kDD1), a1, __fmul_rn(__ldg(coef + kDD2), a2)));
-      s[j * n3 + p] = __fadd_rn(sp[j], dj);  // Drift
+      s[j * n3 + p] = __fadd_rn(s[j * n3 + p], dj);  // Drift
     } else {
       vj = __fadd_rn(vj, fmaf(__ldg(coef + kTD1), a1, __fmul_rn(__ldg(coef + kTD2), a2)));  // L+ (eq. Lops)
     }
     v[j * n3 + p] = vj;
   }
+}
+
+// Gather at particle p (lattice order, its cells from s), then the kick/drift of `mode` (0, 1)
+// or (mode 2) the gathered force alone into gout [3][np^3].
+__device__ __forceinline__ void gather_kick_drift_body(const Geometry& g, const float* __restrict__ fmesh,
+                                                       float* __restrict__ s, float* __restrict__ v,
+                                                       const float* __restrict__ s1, const float* __restrict__ s2,
+                                                       const float* __restrict__ coef, int mode,
+                                                       float* __restrict__ gout, int64_t p) {
+  int ix, iy, iz;
+  lattice_index(g, p, ix, iy, iz);
+  int c[3], t[3];
+  fixed_axis(g, ix, s[p], c[0], t[0]);
+  fixed_axis(g, iy, s[g.np3 + p], c[1], t[1]);
+  fixed_axis(g, iz, s[2 * g.np3 + p], c[2], t[2]);
+  float f[3];
+  gather_force(g, fmesh, c, t, f);
+  if (mode == 2) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gout[j * g.np3 + p] = f[j];
+    return;
+  }
+  kick_drift_update(g, s, v, s1, s2, coef, mode, p, f);
 }
 
 }  // namespace cola

@@ -222,6 +222,44 @@ __global__ void __launch_bounds__(256) k_gather_kick_drift(Geometry g, const flo
   if (p < g.np3) gather_kick_drift_body(g, fmesh, s, v, s1, s2, coef, mode, gout, p);
 }
 
+// Gather in bin order: thread i takes the particle p = idx[i] of bin position i, whose cells
+// are the fixed-point coordinates the scatter stored there (equal to fixed_axis of the current
+// s), so the threads of a block read neighbouring mesh rows however clustered the particles
+// are; the force goes to fj[p].
+__global__ void __launch_bounds__(256) k_gather_binned(Geometry g, const float* __restrict__ fmesh,
+                                                        const unsigned* __restrict__ idx,
+                                                        const uint32_t* __restrict__ coords, float* __restrict__ f0,
+                                                        float* __restrict__ f1, float* __restrict__ f2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.np3) return;
+  const int64_t p = __ldg(idx + i);
+  const uint32_t fmask = (1u << g.fbits) - 1u;
+  int c[3], t[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const uint32_t fx = __ldg(coords + d * g.np3 + i);
+    c[d] = (int)(fx >> g.fbits);
+    t[d] = (int)(fx & fmask);
+  }
+  float f[3];
+  gather_force(g, fmesh, c, t, f);
+  f0[p] = f[0];
+  f1[p] = f[1];
+  f2[p] = f[2];
+}
+
+// Kick/drift in lattice order with the gathered force fj[p].
+__global__ void __launch_bounds__(256) k_kick_drift(Geometry g, const float* __restrict__ f0,
+                                                     const float* __restrict__ f1, const float* __restrict__ f2,
+                                                     float* __restrict__ s, float* __restrict__ v,
+                                                     const float* __restrict__ s1, const float* __restrict__ s2,
+                                                     const float* __restrict__ coef, int mode) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np3) return;
+  const float f[3] = {f0[p], f1[p], f2[p]};
+  kick_drift_update(g, s, v, s1, s2, coef, mode, p, f);
+}
+
 // ---- launchers ------------------------------------------------------------------------------------
 static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
@@ -301,6 +339,22 @@ int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, fl
                              const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st) {
   { LaunchScope ls_("gather_kick_drift", st);
   k_gather_kick_drift<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, s, v, s1, s2, coef_row, mode, gout); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_gather_binned(const Geometry& g, const float* fmesh, const unsigned* idx, const uint32_t* coords,
+                         float* f0, float* f1, float* f2, cudaStream_t st) {
+  { LaunchScope ls_("gather_binned", st);
+  k_gather_binned<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, idx, coords, f0, f1, f2); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,
+                      const float* s1, const float* s2, const float* coef_row, int mode, cudaStream_t st) {
+  { LaunchScope ls_("kick_drift", st);
+  k_kick_drift<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, f0, f1, f2, s, v, s1, s2, coef_row, mode); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
