@@ -149,11 +149,13 @@ def algorithmic_bytes(name, n_p, ng):
     if name.startswith("fft_x_c2r3"):
         return 3 * (H + n**3 * 4)          # three half spectra in, three real meshes out
     table = {
-        "deposit_4x4": 16 * np3 + 4 * ng3,   # idx + s per particle, delta rows written once
-        "deposit_4x2": 16 * np3 + 4 * ng3,
-        "deposit_2x2": 16 * np3 + 4 * ng3,
+        "deposit_4x4": 12 * np3 + 4 * ng3,   # fixed-point coordinates per particle, delta rows written once
+        "deposit_4x2": 12 * np3 + 4 * ng3,
+        "deposit_2x2": 12 * np3 + 4 * ng3,
         "kspace_force": 4 * 8 * ng * ng * (ng // 2 + 1),
         "gather_kick_drift": 72 * np3 + 12 * ng3,  # s, v, s1, s2 in, s, v out; 3 force meshes once
+        "gather_binned": 28 * np3 + 12 * ng3,  # index + coordinates in, force out; 3 force meshes once
+        "kick_drift": 84 * np3,            # force, s, v, s1, s2 in; s, v out
         "keys": 16 * np3,
         "scatter": 32 * np3,               # key + displacement in; index + fixed-point coordinates out
         "power_bin": 8 * ng * ng * (ng // 2 + 1),
@@ -577,7 +579,7 @@ def ensemble_timing(args, dev, rank, world):
         base = name[len("ens_"):]
         alg = 0
         for n_p, ng, _ in boxes:
-            if base in ("keys", "scatter", "gather_kick_drift"):
+            if base in ("keys", "scatter", "gather_kick_drift", "gather_binned", "kick_drift"):
                 a = algorithmic_bytes(base, n_p, ng)
             elif base == "fft_y":
                 a = algorithmic_bytes(f"fft_cols_{ng}", n_p, ng)

@@ -43,7 +43,7 @@ struct BoxDesc {
 };
 
 enum { kEParticles, kEDeposit, kECols, kEC2r, kENumLists };
-enum { kKKeys, kKScatter, kKDeposit, kKYfwd, kKZgreen, kKYinv, kKC2r, kKGather, kKNum };
+enum { kKKeys, kKScatter, kKDeposit, kKYfwd, kKZgreen, kKYinv, kKC2r, kKGather, kKGatherB, kKKick, kKNum };
 
 constexpr int kEnsMaxBoxes = 4096;
 
@@ -256,6 +256,61 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restr
   }
 }
 
+// Gather in bin order into each box's half-spectrum buffers (free once its force meshes exist):
+// the particles of box b hold bin positions pbase .. pbase + np^3 - 1 (the boxes' bins follow
+// one another and every particle has one bin).
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_gather_binned(const BoxDesc* __restrict__ boxes,
+                                                                 const int* __restrict__ starts, int nbox,
+                                                                 const unsigned* __restrict__ idx,
+                                                                 const uint32_t* __restrict__ coords,
+                                                                 int64_t cstride) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int64_t q = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    if (q < d.g.np3) {
+      const int64_t i = d.pbase + q;
+      const int64_t p = __ldg(idx + i);
+      const uint32_t fmask = (1u << d.g.fbits) - 1u;
+      int c[3], t[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t fx = __ldg(coords + k * cstride + i);
+        c[k] = (int)(fx >> d.g.fbits);
+        t[k] = (int)(fx & fmask);
+      }
+      float f[3];
+      gather_force(d.g, d.F, c, t, f);
+      reinterpret_cast<float*>(d.A)[p] = f[0];
+      reinterpret_cast<float*>(d.Gy)[p] = f[1];
+      reinterpret_cast<float*>(d.Gz)[p] = f[2];
+    }
+  }
+}
+
+// Kick/drift in lattice order with the forces of ke_gather_binned.
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ke_kick_drift(const BoxDesc* __restrict__ boxes,
+                                                              const int* __restrict__ starts, int nbox,
+                                                              float* __restrict__ s, float* __restrict__ v,
+                                                              const float* __restrict__ s1,
+                                                              const float* __restrict__ s2, int step, int mode) {
+  const int total = __ldg(starts + nbox);
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = find_box(starts, nbox, item);
+    const BoxDesc& d = boxes[b];
+    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    if (p < d.g.np3) {
+      const int64_t o = 3 * d.pbase;
+      const float f[3] = {reinterpret_cast<const float*>(d.A)[p], reinterpret_cast<const float*>(d.Gy)[p],
+                          reinterpret_cast<const float*>(d.Gz)[p]};
+      kick_drift_update(d.g, s + o, v + o, s1 + o, s2 + o, d.coef + (size_t)step * kCoef32, mode, p, f);
+    }
+  }
+}
+
 // ---- host side ----------------------------------------------------------------------------------
 // threads per transform of length n in radix variant v
 int host_T(int n, int v) {
@@ -308,6 +363,7 @@ using namespace cola;
 struct cola_ensemble {
   std::vector<cola_plan*> plans;
   int nbox = 0, nsteps = 0, min_ng = 0;
+  bool binned_gather = true;  // every box gathers in bin order (as its single-box plan does)
   std::vector<int64_t> poff, moff;
   std::vector<size_t> plan_off;
   size_t ens_off = 0, ws_bytes = 0;
@@ -371,8 +427,10 @@ int kernel_attrs(cola_ensemble* e) {
   const void* fns[kKNum] = {(const void*)ke_keys<NT>,       (const void*)ke_scatter<NT>,
                             (const void*)ke_deposit<NT, V>, (const void*)ke_cols<NT, 0, V>,
                             (const void*)ke_cols<NT, 1, V>, (const void*)ke_cols<NT, 2, V>,
-                            (const void*)ke_c2r3<NT, V>,    (const void*)ke_gather<NT>};
-  const int lists[kKNum] = {kEParticles, kEParticles, kEDeposit, kECols, kECols, kECols, kEC2r, kEParticles};
+                            (const void*)ke_c2r3<NT, V>,    (const void*)ke_gather<NT>,
+                            (const void*)ke_gather_binned<NT>, (const void*)ke_kick_drift<NT>};
+  const int lists[kKNum] = {kEParticles, kEParticles, kEDeposit,   kECols,     kECols,
+                            kECols,      kEC2r,       kEParticles, kEParticles, kEParticles};
   for (int k = 0; k < kKNum; ++k) {
     if (e->smem[k] > 227 * 1024) return fail(COLA_EUNSUPPORTED, "ensemble kernel: shared memory request too large");
     COLA_CUDA_CHECK(cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem[k]));
@@ -517,9 +575,20 @@ int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1
   const int nb = e->nbox;
   const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
   const int mode = step == e->nsteps ? 1 : 0;
-  {
+  if (!e->binned_gather) {
     LaunchScope ls_("ens_gather_kick_drift", st);
     ke_gather<NT><<<e->grid[kKGather], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
+    COLA_LAUNCH_CHECK();
+    return COLA_OK;
+  }
+  {
+    LaunchScope ls_("ens_gather_binned", st);
+    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->idx, e->coords, e->poff[nb]);
+  }
+  COLA_LAUNCH_CHECK();
+  {
+    LaunchScope ls_("ens_kick_drift", st);
+    ke_kick_drift<NT><<<e->grid[kKKick], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
@@ -646,6 +715,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
       return fail(rc, why);
     }
     e->plans.push_back(p);
+    e->binned_gather = e->binned_gather && p->binned_gather;
     e->poff[b + 1] = e->poff[b] + p->geo.np3;
     e->moff[b + 1] = e->moff[b] + p->ng3;
     e->plan_off[b] = off;
