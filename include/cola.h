@@ -311,8 +311,9 @@ int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola
  * nbins <= the smallest ng of the ensemble. */
 int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
                         int64_t* nmodes, cola_stream stream);
-/* Autotuner: times the binning and mesh passes of one force evaluation at displacements s
- * (read only) for each of the COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
+/* Autotuner: times one force evaluation without the particle update (binning, mesh passes and
+ * the gather into scratch) at displacements s (read only) for each of the
+ * COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
  * repetitions after one warm-up, CUDA events on `stream`; synchronises), keeps the fastest
  * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
  * milliseconds of each candidate, in the order threads in {128, 256} x tile_shape in {0, 1}

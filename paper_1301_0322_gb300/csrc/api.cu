@@ -37,8 +37,7 @@ static size_t layout(cola_plan* p, char* base) {
   w.coef = (float*)take(sizeof(float) * kCoef32 * (p->cfg.nsteps + 1));
   w.err = (int*)take(sizeof(int) * 4);
   w.keys = (int*)take(sizeof(int) * np3);
-  w.idx = (unsigned*)take(sizeof(unsigned) * np3);
-  w.coords = (uint32_t*)take(sizeof(uint32_t) * 3 * np3);
+  w.rec = (uint4*)take(sizeof(uint4) * np3);
   w.counts = (int*)take(sizeof(int) * p->tiles.nbins);
   w.offsets = (int*)take(sizeof(int) * (p->tiles.nbins + 1));
   w.cursor = (int*)take(sizeof(int) * p->tiles.nbins);
@@ -71,14 +70,14 @@ static int check_ws(const cola_plan* p) {
 
 static int padded_half(int n) { return ((n / 2 + 1) + 3) / 4 * 4; }
 
-// particle binning for positions s: keys -> counts -> offsets -> idx
+// particle binning for positions s: keys -> counts -> offsets -> bin-ordered records
 static int bin_particles(cola_plan* p, const float* s, cudaStream_t st) {
   Workspace& w = p->ws;
   int rc = launch_keys(p->geo, p->tiles, s, w.keys, w.counts, w.err, st);
   if (rc) return rc;
   rc = launch_scan(p->tiles, w.counts, w.offsets, w.cursor, w.scan_blocks, st);
   if (rc) return rc;
-  return launch_scatter(p->geo, s, w.keys, w.cursor, w.idx, w.coords, st);
+  return launch_scatter(p->geo, s, w.keys, w.cursor, w.rec, st);
 }
 
 // unit force meshes g_j (freal[j]) for positions s
@@ -86,7 +85,7 @@ static int force_meshes(cola_plan* p, const float* s, cudaStream_t st) {
   Workspace& w = p->ws;
   int rc = bin_particles(p, s, st);
   if (rc) return rc;
-  return launch_force_passes(p->geo, p->tiles, w.coords, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
+  return launch_force_passes(p->geo, p->tiles, w.rec, w.offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
                              p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
 }
 
@@ -325,7 +324,7 @@ int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1
   // the gathered forces go to the half-spectrum buffers, free once the force meshes exist
   float* f[3] = {reinterpret_cast<float*>(w.meshA), reinterpret_cast<float*>(w.meshG[1]),
                  reinterpret_cast<float*>(w.meshG[2])};
-  if ((rc = launch_gather_binned(plan->geo, w.freal, w.idx, w.coords, f[0], f[1], f[2], st))) return rc;
+  if ((rc = launch_gather_binned(plan->geo, w.freal, w.rec, f[0], f[1], f[2], st))) return rc;
   return launch_kick_drift(plan->geo, f[0], f[1], f[2], s, v, s1, s2, coef, mode, st);
 }
 
@@ -337,7 +336,7 @@ int cola_force(cola_plan* plan, const float* s, float* g, cola_stream stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = force_meshes(plan, s, st))) return rc;
   const int64_t n3 = plan->geo.np3;
-  return launch_gather_binned(plan->geo, plan->ws.freal, plan->ws.idx, plan->ws.coords, g, g + n3, g + 2 * n3, st);
+  return launch_gather_binned(plan->geo, plan->ws.freal, plan->ws.rec, g, g + n3, g + 2 * n3, st);
 }
 
 int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta, cola_stream stream) {
@@ -347,7 +346,7 @@ int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta
   if (!s || (!rho_fix && !delta)) return fail(COLA_EINVAL, "null array");
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = bin_particles(plan, s, st))) return rc;
-  return launch_deposit(plan->geo, plan->tiles, plan->ws.coords, plan->ws.offsets, rho_fix, delta, plan->ws.err, st);
+  return launch_deposit(plan->geo, plan->tiles, plan->ws.rec, plan->ws.offsets, rho_fix, delta, plan->ws.err, st);
 }
 
 int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, double* pk, int64_t* nmodes,

@@ -55,8 +55,9 @@ struct Workspace {
   float* freal = nullptr;   // 3 x ng^3 force meshes (freal[0..ng^3) doubles as delta)
   // particle binning
   int* keys = nullptr;
-  unsigned* idx = nullptr;
-  uint32_t* coords = nullptr;  // [3][np^3] fixed-point CIC coordinates in bin order
+  // [np^3] in bin order: the particle's fixed-point CIC coordinates f_x, f_y, f_z and its
+  // lattice index (one 16-byte record, written and read with one access)
+  uint4* rec = nullptr;
   int* counts = nullptr;    // nbins
   int* offsets = nullptr;   // nbins + 1
   int* cursor = nullptr;    // nbins
@@ -123,23 +124,23 @@ int fft3d_c2r(int n, int P, float2* in_destroyed, float* out, const float2* tw, 
 int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st);
 int scan_block_count(const Tiles& t);
 int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* block_sums, cudaStream_t st);
-int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, unsigned* idx, uint32_t* coords,
+int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, uint4* rec,
                    cudaStream_t st);
-int launch_deposit(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+int launch_deposit(const Geometry& g, const Tiles& t, const uint4* rec, const int* offsets, int64_t* rho,
                    float* delta, int* err, cudaStream_t st);
 int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk, float2* gx, float2* gy, float2* gz,
                         cudaStream_t st);
 // the fused mesh passes of one force evaluation (pm_fft_kernels.cu): deposit + x r2c, y pass,
 // z pass with the Green's function, inverse y passes, inverse x passes -> F [3][ng^3]
-int launch_force_passes(const Geometry& g, const Tiles& tl, const uint32_t* coords, const int* offsets,
+int launch_force_passes(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                         float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv, const float2* tw,
                         int* err, cudaStream_t st);
 // mode 0: kick + drift, 1: kick + L+ (last force evaluation), 2: write the gathered unit force to gout
 int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, float* v, const float* s1,
                              const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st);
-// the gather in bin order of the last binning (idx, coords) into fj[p], and the kick/drift in
+// the gather in bin order of the last binning (records rec) into fj[p], and the kick/drift in
 // lattice order from those forces
-int launch_gather_binned(const Geometry& g, const float* fmesh, const unsigned* idx, const uint32_t* coords,
+int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec,
                          float* f0, float* f1, float* f2, cudaStream_t st);
 int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,
                       const float* s1, const float* s2, const float* coef_row, int mode, cudaStream_t st);

@@ -5,12 +5,12 @@
 // Each box keeps a full single-box plan (its coefficient table, twiddles and mesh buffers);
 // the ensemble adds a description of every box for the device, the shared particle-sort
 // buffers and the work lists.  The bins of all boxes form one array (box b's bins start at
-// bin_base), so one scan serves every box, and box b's sorted particle indices land in
-// positions [poff[b], poff[b+1]) of the shared index array.
+// bin_base), so one scan serves every box, and box b's bin-ordered particle records land in
+// positions [poff[b], poff[b+1]) of the shared record array.
 //
 // One step (eq. ALCtimestep) = keys, 3 scan phases, scatter, deposit + x r2c, y pass, z pass
-// with the Green's function, inverse y passes, inverse x passes, gather + kick + drift:
-// 11 launches for the whole ensemble, recorded once per step as a CUDA graph.
+// with the Green's function, inverse y passes, inverse x passes, gather in bin order, kick +
+// drift: 12 launches for the whole ensemble, recorded once per step as a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -86,44 +86,42 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __restrict__ boxes,
                                                            const int* __restrict__ starts, int nbox,
                                                            const float* __restrict__ s, const int* __restrict__ keys,
-                                                           int* __restrict__ cursor, unsigned* __restrict__ idx,
-                                                           uint32_t* __restrict__ coords, int64_t cstride) {
+                                                           int* __restrict__ cursor, uint4* __restrict__ rec) {
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int b = find_box(starts, nbox, item);
     const BoxDesc& d = boxes[b];
     const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
-    scatter_body(d.g, s + 3 * d.pbase, p, p < d.g.np3, keys + d.pbase, cursor, idx, coords, cstride);
+    scatter_body(d.g, s + 3 * d.pbase, p, p < d.g.np3, keys + d.pbase, cursor, rec);
   }
 }
 
 // One tile of one box.  Not inlined: every (size, tile) instantiation gets its own register
 // allocation instead of the union of all of them.
 template <int N, int TY, int TZ, class CM>
-__device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const uint32_t* __restrict__ coords,
-                                          int64_t cstride, const int* __restrict__ offsets, int tile) {
+__device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const uint4* __restrict__ rec,
+                                          const int* __restrict__ offsets, int tile) {
   extern __shared__ __align__(16) unsigned long long ens_smem[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ, CM>(d->g, d->tl, coords, cstride, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile,
-                               ens_smem, ints);
+  deposit_fftx_body<N, TY, TZ, CM>(d->g, d->tl, rec, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile, ens_smem,
+                                   ints);
 }
 
 template <int N, int NT, int V>
-__device__ __forceinline__ void deposit_item(const BoxDesc* d, const uint32_t* coords, int64_t cstride,
-                                             const int* offsets, int tile) {
+__device__ __forceinline__ void deposit_item(const BoxDesc* d, const uint4* rec, const int* offsets, int tile) {
   using CM = FFTConfV<N / 2, V>;
   constexpr int ROWS = NT / CM::T;
   constexpr int TY0 = ens_tile_ty(ROWS, 0), TY1 = ens_tile_ty(ROWS, 1);
   if (d->tl.ty == TY0)
-    deposit_tile<N, TY0, ROWS / TY0, CM>(d, coords, cstride, offsets, tile);
+    deposit_tile<N, TY0, ROWS / TY0, CM>(d, rec, offsets, tile);
   else
-    deposit_tile<N, TY1, ROWS / TY1, CM>(d, coords, cstride, offsets, tile);
+    deposit_tile<N, TY1, ROWS / TY1, CM>(d, rec, offsets, tile);
 }
 
 template <int NT, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __restrict__ boxes,
                                                            const int* __restrict__ starts, int nbox,
-                                                           const uint32_t* __restrict__ coords, int64_t cstride,
+                                                           const uint4* __restrict__ rec,
                                                            const int* __restrict__ offsets) {
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -134,7 +132,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __rest
     switch (d->g.ng) {
 #define X(N)                                              \
   case N:                                                 \
-    deposit_item<N, NT, V>(d, coords, cstride, ob, local); \
+    deposit_item<N, NT, V>(d, rec, ob, local);            \
     break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -262,24 +260,22 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restr
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_gather_binned(const BoxDesc* __restrict__ boxes,
                                                                  const int* __restrict__ starts, int nbox,
-                                                                 const unsigned* __restrict__ idx,
-                                                                 const uint32_t* __restrict__ coords,
-                                                                 int64_t cstride) {
+                                                                 const uint4* __restrict__ rec) {
   const int total = __ldg(starts + nbox);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int b = find_box(starts, nbox, item);
     const BoxDesc& d = boxes[b];
     const int64_t q = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
     if (q < d.g.np3) {
-      const int64_t i = d.pbase + q;
-      const int64_t p = __ldg(idx + i);
+      const uint4 r = __ldg(rec + d.pbase + q);
+      const int64_t p = r.w;
       const uint32_t fmask = (1u << d.g.fbits) - 1u;
+      const uint32_t fq[3] = {r.x, r.y, r.z};
       int c[3], t[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const uint32_t fx = __ldg(coords + k * cstride + i);
-        c[k] = (int)(fx >> d.g.fbits);
-        t[k] = (int)(fx & fmask);
+        c[k] = (int)(fq[k] >> d.g.fbits);
+        t[k] = (int)(fq[k] & fmask);
       }
       float f[3];
       gather_force(d.g, d.F, c, t, f);
@@ -371,8 +367,7 @@ struct cola_ensemble {
   void* ws_base = nullptr;
   // shared device buffers
   int* keys = nullptr;
-  unsigned* idx = nullptr;
-  uint32_t* coords = nullptr;  // [3][all particles] fixed-point CIC coordinates in bin order
+  uint4* rec = nullptr;  // [all particles] bin-ordered records (fixed-point coordinates, lattice index)
   int* counts = nullptr;
   int* offsets = nullptr;
   int* cursor = nullptr;
@@ -534,14 +529,12 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   if (rc) return rc;
   {
     LaunchScope ls_("ens_scatter", st);
-    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->cursor, e->idx, e->coords,
-                                                        e->poff[nb]);
+    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->cursor, e->rec);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_deposit_fftx", st);
-    ke_deposit<NT, V><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->coords, e->poff[nb],
-                                                                        e->offsets);
+    ke_deposit<NT, V><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->rec, e->offsets);
   }
   COLA_LAUNCH_CHECK();
   {
@@ -583,7 +576,7 @@ int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1
   }
   {
     LaunchScope ls_("ens_gather_binned", st);
-    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->idx, e->coords, e->poff[nb]);
+    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->rec);
   }
   COLA_LAUNCH_CHECK();
   {
@@ -602,10 +595,27 @@ int enqueue_step_any(cola_ensemble* e, int step, float* s, float* v, const float
   return r ? enqueue_step<256, 1>(e, step, s, v, s1, s2, st) : enqueue_step<256, 0>(e, step, s, v, s1, s2, st);
 }
 
-int enqueue_mesh_any(cola_ensemble* e, const float* s, cudaStream_t st) {
+// The force evaluation without the particle update (what the autotuner times): the binning and
+// mesh passes, and the gather in bin order, whose mesh locality depends on the tile shape (it
+// writes only the half-spectrum buffers, so the particle state is left untouched).
+template <int NT, int V>
+int enqueue_force(cola_ensemble* e, const float* s, cudaStream_t st) {
+  int rc = enqueue_mesh_passes<NT, V>(e, s, st);
+  if (rc || !e->binned_gather) return rc;
+  const int nb = e->nbox;
+  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
+  {
+    LaunchScope ls_("ens_gather_binned", st);
+    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->rec);
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int enqueue_force_any(cola_ensemble* e, const float* s, cudaStream_t st) {
   const bool r = e->tuning.radix != 0;
-  if (e->tuning.threads == 128) return r ? enqueue_mesh_passes<128, 1>(e, s, st) : enqueue_mesh_passes<128, 0>(e, s, st);
-  return r ? enqueue_mesh_passes<256, 1>(e, s, st) : enqueue_mesh_passes<256, 0>(e, s, st);
+  if (e->tuning.threads == 128) return r ? enqueue_force<128, 1>(e, s, st) : enqueue_force<128, 0>(e, s, st);
+  return r ? enqueue_force<256, 1>(e, s, st) : enqueue_force<256, 0>(e, s, st);
 }
 
 int check_ens(const cola_ensemble* e) {
@@ -736,8 +746,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
   Tiles all{};
   all.nbins = e->max_bins_total;
   off += align256(sizeof(int) * np_all);                   // keys
-  off += align256(sizeof(unsigned) * np_all);              // idx
-  off += align256(sizeof(uint32_t) * 3 * np_all);          // coords
+  off += align256(sizeof(uint4) * np_all);                 // bin-ordered records
   off += align256(sizeof(int) * all.nbins);                // counts
   off += align256(sizeof(int) * (all.nbins + 1));          // offsets
   off += align256(sizeof(int) * all.nbins);                // cursor
@@ -782,8 +791,7 @@ int cola_ensemble_set_workspace(cola_ensemble* ens, void* dev_ptr, size_t bytes,
   Tiles all{};
   all.nbins = ens->max_bins_total;
   ens->keys = (int*)take(sizeof(int) * np_all);
-  ens->idx = (unsigned*)take(sizeof(unsigned) * np_all);
-  ens->coords = (uint32_t*)take(sizeof(uint32_t) * 3 * np_all);
+  ens->rec = (uint4*)take(sizeof(uint4) * np_all);
   ens->counts = (int*)take(sizeof(int) * all.nbins);
   ens->offsets = (int*)take(sizeof(int) * (all.nbins + 1));
   ens->cursor = (int*)take(sizeof(int) * all.nbins);
@@ -915,12 +923,12 @@ int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_en
   for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
     ens->tuning = cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1};
     if ((rc = configure(ens, st))) break;
-    if ((rc = enqueue_mesh_any(ens, s, st))) break;  // warm-up
+    if ((rc = enqueue_force_any(ens, s, st))) break;  // warm-up
     if (cudaEventRecord(e0, st) != cudaSuccess) {
       rc = fail(COLA_ECUDA, "event record");
       break;
     }
-    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_mesh_any(ens, s, st);
+    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_force_any(ens, s, st);
     if (rc) break;
     float el = 0.f;
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

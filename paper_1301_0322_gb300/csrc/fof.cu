@@ -94,12 +94,13 @@ __device__ __forceinline__ int64_t min_image(int64_t d, int64_t period) {
   return d;
 }
 
-__global__ void k_fof_link(Geometry g, const uint32_t* __restrict__ f, const int* __restrict__ offsets, int csize,
+__global__ void k_fof_link(Geometry g, const uint4* __restrict__ rec, const int* __restrict__ offsets, int csize,
                            int nc, int64_t den2, int64_t lim, int* __restrict__ parent, int* __restrict__ err) {
   const int64_t n = g.np3;
   const int64_t period = (int64_t)g.ng << g.fbits;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t fx = f[i], fy = f[n + i], fz = f[2 * n + i];
+    const uint4 qi = rec[i];
+    const int64_t fx = qi.x, fy = qi.y, fz = qi.z;
     const int cx = (int)(fx >> g.fbits) / csize, cy = (int)(fy >> g.fbits) / csize, cz = (int)(fz >> g.fbits) / csize;
     bool ok = true;
     for (int dz = -1; dz <= 1; ++dz) {
@@ -111,9 +112,10 @@ __global__ void k_fof_link(Geometry g, const uint32_t* __restrict__ f, const int
           const int cell = (zz * nc + yy) * nc + xx;
           const int j1 = offsets[cell + 1];
           for (int j = max(offsets[cell], (int)i + 1); j < j1; ++j) {
-            const int64_t ex = min_image((int64_t)f[j] - fx, period);
-            const int64_t ey = min_image((int64_t)f[n + j] - fy, period);
-            const int64_t ez = min_image((int64_t)f[2 * n + j] - fz, period);
+            const uint4 qj = rec[j];
+            const int64_t ex = min_image((int64_t)qj.x - fx, period);
+            const int64_t ey = min_image((int64_t)qj.y - fy, period);
+            const int64_t ez = min_image((int64_t)qj.z - fz, period);
             const int64_t d2 = ex * ex + ey * ey + ez * ez;
             if (den2 * d2 < lim) ok = fof_union(parent, (int)i, j) && ok;
           }
@@ -124,23 +126,23 @@ __global__ void k_fof_link(Geometry g, const uint32_t* __restrict__ f, const int
   }
 }
 
-__global__ void k_fof_groups(int64_t n, const unsigned* __restrict__ idx, int* __restrict__ parent,
+__global__ void k_fof_groups(int64_t n, const uint4* __restrict__ rec, int* __restrict__ parent,
                              int* __restrict__ gsize, int* __restrict__ minp) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int r = fof_find(parent, (int)i);
     parent[i] = r;
     atomicAdd(gsize + r, 1);
-    atomicMin(minp + r, (int)idx[i]);
+    atomicMin(minp + r, (int)rec[i].w);
   }
 }
 
-__global__ void k_fof_output(int64_t n, const unsigned* __restrict__ idx, const int* __restrict__ parent,
+__global__ void k_fof_output(int64_t n, const uint4* __restrict__ rec, const int* __restrict__ parent,
                              const int* __restrict__ gsize, const int* __restrict__ minp, int nmin, Thresholds thr,
                              int* __restrict__ group, int* __restrict__ size, unsigned long long* __restrict__ n_ge) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int r = parent[i];
     const int gs = gsize[r];
-    const unsigned p = idx[i];
+    const unsigned p = rec[i].w;
     if (size) size[p] = gs;
     if (group) group[p] = gs >= nmin ? minp[r] : -1;
     if (r == (int)i && gs >= nmin)
@@ -205,7 +207,7 @@ extern "C" int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t 
   COLA_LAUNCH_CHECK();
   int rc = launch_scan(cells, counts, offsets, cursor, scan_blocks, st);
   if (rc) return rc;
-  if ((rc = launch_scatter(g, s, w.keys, cursor, w.idx, w.coords, st))) return rc;
+  if ((rc = launch_scatter(g, s, w.keys, cursor, w.rec, st))) return rc;
   {
     LaunchScope ls_("fof_init", st);
     k_fof_init<<<grid_of(n), 256, 0, st>>>(n, parent, gsize, minp);
@@ -215,18 +217,18 @@ extern "C" int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t 
   const int64_t lim = (int64_t)b_num * b_num * sfix * sfix;
   {
     LaunchScope ls_("fof_link", st);
-    k_fof_link<<<grid_of(n), 256, 0, st>>>(g, w.coords, offsets, csize, nc, (int64_t)b_den * b_den, lim, parent,
+    k_fof_link<<<grid_of(n), 256, 0, st>>>(g, w.rec, offsets, csize, nc, (int64_t)b_den * b_den, lim, parent,
                                            w.err);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("fof_groups", st);
-    k_fof_groups<<<grid_of(n), 256, 0, st>>>(n, w.idx, parent, gsize, minp);
+    k_fof_groups<<<grid_of(n), 256, 0, st>>>(n, w.rec, parent, gsize, minp);
   }
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("fof_output", st);
-    k_fof_output<<<grid_of(n), 256, 0, st>>>(n, w.idx, parent, gsize, minp, nmin, thr, group, size,
+    k_fof_output<<<grid_of(n), 256, 0, st>>>(n, w.rec, parent, gsize, minp, nmin, thr, group, size,
                                              reinterpret_cast<unsigned long long*>(n_ge));
   }
   COLA_LAUNCH_CHECK();

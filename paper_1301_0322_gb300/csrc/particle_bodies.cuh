@@ -39,13 +39,13 @@ __device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, co
   if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
-// Counting-sort scatter: pos = cursor[keys[p]]++ (one atomic per distinct key in the warp),
-// idx[pos] = p, and the particle's fixed-point CIC coordinates f_d = (cell << F) | t (x, y, z;
-// each < ng 2^F <= 2^31) at coords[d * cstride + pos], so the deposit reads them in bin order.
+// Counting-sort scatter: pos = cursor[keys[p]]++ (one atomic per distinct key in the warp) and
+// rec[pos] = (f_x, f_y, f_z, p): the particle's fixed-point CIC coordinates f_d = (cell << F) | t
+// (each < ng 2^F <= 2^31) and its lattice index, so the deposit and the gather read them in bin
+// order with one 16-byte access.
 __device__ __forceinline__ void scatter_body(const Geometry& g, const float* __restrict__ s, int64_t p, bool live,
                                              const int* __restrict__ keys, int* __restrict__ cursor,
-                                             unsigned* __restrict__ idx, uint32_t* __restrict__ coords,
-                                             int64_t cstride) {
+                                             uint4* __restrict__ rec) {
   const int key = live ? keys[p] : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
@@ -55,17 +55,17 @@ __device__ __forceinline__ void scatter_body(const Geometry& g, const float* __r
   base = __shfl_sync(peers, base, leader);
   const int rank = __popc(peers & ((1u << lane) - 1u));
   if (live) {
-    const int pos = base + rank;
-    idx[pos] = (unsigned)p;
     int ix, iy, iz;
     lattice_index(g, p, ix, iy, iz);
     const int li[3] = {ix, iy, iz};
+    uint32_t f[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int c, t;
       fixed_axis(g, li[d], s[d * g.np3 + p], c, t);
-      coords[d * cstride + pos] = ((uint32_t)c << g.fbits) | (uint32_t)t;
+      f[d] = ((uint32_t)c << g.fbits) | (uint32_t)t;
     }
+    rec[base + rank] = make_uint4(f[0], f[1], f[2], (uint32_t)p);
   }
 }
 

@@ -48,10 +48,9 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
 // block: one tile of TY x TZ rows (T(N/2) * TY * TZ threads); acc: max(TY TZ N, TY TZ LD) x 8
 // bytes of shared memory (the cells' low 32-bit words, then their high words; afterwards the
 // rows' transform buffers); ints: 28 ints of shared memory
-// coords: [3][cstride] fixed-point CIC coordinates in bin order (offsets index them directly)
+// rec: the bin-ordered particle records (fixed-point CIC coordinates; offsets index them directly)
 template <int N, int TY, int TZ, class CM = FFTConf<N / 2>>
-__device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl,
-                                                  const uint32_t* __restrict__ coords, int64_t cstride,
+__device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl, const uint4* __restrict__ rec,
                                                   const int* __restrict__ offsets, float2* __restrict__ out, int P,
                                                   const float2* __restrict__ tw, float dscale, int* __restrict__ err,
                                                   int tile, unsigned long long* acc, int* ints) {
@@ -102,10 +101,10 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
         int r = 0;
 #pragma unroll
         for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
-        const int64_t pos = rbeg[r] + (i - rpre[r]);
-        f[u][0] = __ldg(coords + pos);
-        f[u][1] = __ldg(coords + cstride + pos);
-        f[u][2] = __ldg(coords + 2 * cstride + pos);
+        const uint4 q = __ldg(rec + rbeg[r] + (i - rpre[r]));
+        f[u][0] = q.x;
+        f[u][1] = q.y;
+        f[u][2] = q.z;
       }
     }
 #pragma unroll

@@ -18,12 +18,12 @@ namespace cola {
 // ---- single-box kernels ------------------------------------------------------------------------
 template <int N, int TY, int TZ>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, (512 / (FFTConf<N / 2>::T * TY * TZ)) > 0 ? 512 / (FFTConf<N / 2>::T * TY * TZ) : 1)
-    k_deposit_fftx(Geometry g, Tiles tl, const uint32_t* __restrict__ coords, const int* __restrict__ offsets,
+    k_deposit_fftx(Geometry g, Tiles tl, const uint4* __restrict__ rec, const int* __restrict__ offsets,
                    float2* __restrict__ out, int P, const float2* __restrict__ tw, float dscale,
                    int* __restrict__ err) {
   extern __shared__ unsigned long long acc[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ>(g, tl, coords, g.np3, offsets, out, P, tw, dscale, err, blockIdx.x, acc, ints);
+  deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, dscale, err, blockIdx.x, acc, ints);
 }
 
 template <int N>
@@ -101,7 +101,7 @@ static const char* flabel(int kind) {
 }
 
 template <int N>
-static int force_passes_t(const Geometry& g, const Tiles& tl, const uint32_t* coords, const int* offsets,
+static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                           float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv,
                           const float2* tw, int* err, cudaStream_t st) {
   constexpr int M = N / 2, W = green_width<N>(), nh = N / 2 + 1;
@@ -116,13 +116,13 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint32_t* co
       const size_t smem = sizeof(unsigned long long) * 8 * std::max(N, xrow_ld<M>());
       if ((rc = set_smem(k_deposit_fftx<N, 4, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
-      k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, coords, offsets, A, P, tw,
+      k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, rec, offsets, A, P, tw,
                                                                                   dscale, err);
     } else if (tl.ty == 2 && tl.tz == 2) {
       const size_t smem = sizeof(unsigned long long) * 4 * std::max(N, xrow_ld<M>());
       if ((rc = set_smem(k_deposit_fftx<N, 2, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
-      k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, coords, offsets, A, P, tw,
+      k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, rec, offsets, A, P, tw,
                                                                                   dscale, err);
     } else {
       return fail(COLA_EUNSUPPORTED, "fused deposit: unsupported tile shape");
@@ -175,13 +175,13 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint32_t* co
   return COLA_OK;
 }
 
-int launch_force_passes(const Geometry& g, const Tiles& tl, const uint32_t* coords, const int* offsets,
+int launch_force_passes(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                         float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv, const float2* tw,
                         int* err, cudaStream_t st) {
   switch (g.ng) {
 #define X(N) \
   case N:    \
-    return force_passes_t<N>(g, tl, coords, offsets, A, Gy, Gz, F, P, box, deconv, tw, err, st);
+    return force_passes_t<N>(g, tl, rec, offsets, A, Gy, Gz, F, P, box, deconv, tw, err, st);
     X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048)
 #undef X
     default:

@@ -84,18 +84,18 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ co
 }
 
 __global__ void k_scatter(Geometry g, const float* __restrict__ s, const int* __restrict__ keys,
-                          int* __restrict__ cursor, unsigned* __restrict__ idx, uint32_t* __restrict__ coords) {
+                          int* __restrict__ cursor, uint4* __restrict__ rec) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  scatter_body(g, s, p, p < g.np3, keys, cursor, idx, coords, g.np3);
+  scatter_body(g, s, p, p < g.np3, keys, cursor, rec);
 }
 
 // ---- deposit ----------------------------------------------------------------------------------
-// One block per tile of TY x TZ mesh rows (whole x extent).  It reads the fixed-point CIC
-// coordinates (stored by the scatter in bin order) of the particles binned to the tile and to
+// One block per tile of TY x TZ mesh rows (whole x extent).  It reads the bin-ordered records
+// (fixed-point CIC coordinates, stored by the scatter) of the particles binned to the tile and to
 // the boundary regions of its three lower neighbours, accumulates exact int64 CIC weights in
 // shared memory and writes the rows once (int64 and/or float overdensity).
 template <int TY, int TZ>
-__global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uint32_t* __restrict__ coords,
+__global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uint4* __restrict__ rec,
                                                  const int* __restrict__ offsets, int64_t* __restrict__ rho,
                                                  float* __restrict__ delta, float dscale, int* __restrict__ err) {
   extern __shared__ unsigned long long acc[];
@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uin
     for (int k = 1; k < 9; ++k) r += (i >= rpre[k]) ? 1 : 0;
     const int64_t pos = rbeg[r] + (i - rpre[r]);
     const uint32_t fmask = (uint32_t)one - 1u;
-    const uint32_t fx = __ldg(coords + pos), fy = __ldg(coords + g.np3 + pos), fz = __ldg(coords + 2 * g.np3 + pos);
+    const uint4 q = __ldg(rec + pos);
+    const uint32_t fx = q.x, fy = q.y, fz = q.z;
     const int cx = (int)(fx >> g.fbits), tx = (int)(fx & fmask);
     const int cy = (int)(fy >> g.fbits), ty = (int)(fy & fmask);
     const int cz = (int)(fz >> g.fbits), tz = (int)(fz & fmask);
@@ -222,24 +223,24 @@ __global__ void __launch_bounds__(256) k_gather_kick_drift(Geometry g, const flo
   if (p < g.np3) gather_kick_drift_body(g, fmesh, s, v, s1, s2, coef, mode, gout, p);
 }
 
-// Gather in bin order: thread i takes the particle p = idx[i] of bin position i, whose cells
-// are the fixed-point coordinates the scatter stored there (equal to fixed_axis of the current
-// s), so the threads of a block read neighbouring mesh rows however clustered the particles
-// are; the force goes to fj[p].
+// Gather in bin order: thread i takes the particle of bin position i from its record (lattice
+// index p and the fixed-point coordinates, which equal fixed_axis of the current s), so the
+// threads of a block read neighbouring mesh rows however clustered the particles are; the
+// force goes to fj[p].
 __global__ void __launch_bounds__(256) k_gather_binned(Geometry g, const float* __restrict__ fmesh,
-                                                        const unsigned* __restrict__ idx,
-                                                        const uint32_t* __restrict__ coords, float* __restrict__ f0,
+                                                        const uint4* __restrict__ rec, float* __restrict__ f0,
                                                         float* __restrict__ f1, float* __restrict__ f2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.np3) return;
-  const int64_t p = __ldg(idx + i);
+  const uint4 q = __ldg(rec + i);
+  const int64_t p = q.w;
   const uint32_t fmask = (1u << g.fbits) - 1u;
+  const uint32_t fq[3] = {q.x, q.y, q.z};
   int c[3], t[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const uint32_t fx = __ldg(coords + d * g.np3 + i);
-    c[d] = (int)(fx >> g.fbits);
-    t[d] = (int)(fx & fmask);
+    c[d] = (int)(fq[d] >> g.fbits);
+    t[d] = (int)(fq[d] & fmask);
   }
   float f[3];
   gather_force(g, fmesh, c, t, f);
@@ -292,16 +293,16 @@ int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* blo
   return COLA_OK;
 }
 
-int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, unsigned* idx, uint32_t* coords,
+int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, uint4* rec,
                    cudaStream_t st) {
   { LaunchScope ls_("scatter", st);
-  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, s, keys, cursor, idx, coords); }
+  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, s, keys, cursor, rec); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 
 template <int TY, int TZ>
-static int deposit_t(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+static int deposit_t(const Geometry& g, const Tiles& t, const uint4* rec, const int* offsets, int64_t* rho,
                      float* delta, int* err, cudaStream_t st) {
   const size_t smem = (size_t)TY * TZ * g.ng * sizeof(unsigned long long);
   if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "deposit tile does not fit in shared memory");
@@ -310,16 +311,16 @@ static int deposit_t(const Geometry& g, const Tiles& t, const uint32_t* coords, 
   const double ng3 = (double)g.ng * g.ng * g.ng;
   const float dscale = (float)(ng3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
   { LaunchScope ls_(TY == 2 ? "deposit_2x2" : (TZ == 2 ? "deposit_4x2" : "deposit_4x4"), st);
-  k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, coords, offsets, rho, delta, dscale, err); }
+  k_deposit<TY, TZ><<<t.nty * t.ntz, 256, smem, st>>>(g, t, rec, offsets, rho, delta, dscale, err); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 
-int launch_deposit(const Geometry& g, const Tiles& t, const uint32_t* coords, const int* offsets, int64_t* rho,
+int launch_deposit(const Geometry& g, const Tiles& t, const uint4* rec, const int* offsets, int64_t* rho,
                    float* delta, int* err, cudaStream_t st) {
-  if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, coords, offsets, rho, delta, err, st);
-  if (t.ty == 4 && t.tz == 2) return deposit_t<4, 2>(g, t, coords, offsets, rho, delta, err, st);
-  if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, coords, offsets, rho, delta, err, st);
+  if (t.ty == 4 && t.tz == 4) return deposit_t<4, 4>(g, t, rec, offsets, rho, delta, err, st);
+  if (t.ty == 4 && t.tz == 2) return deposit_t<4, 2>(g, t, rec, offsets, rho, delta, err, st);
+  if (t.ty == 2 && t.tz == 2) return deposit_t<2, 2>(g, t, rec, offsets, rho, delta, err, st);
   return fail(COLA_EUNSUPPORTED, "deposit: unsupported tile shape");
 }
 
@@ -343,10 +344,10 @@ int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, fl
   return COLA_OK;
 }
 
-int launch_gather_binned(const Geometry& g, const float* fmesh, const unsigned* idx, const uint32_t* coords,
+int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec,
                          float* f0, float* f1, float* f2, cudaStream_t st) {
   { LaunchScope ls_("gather_binned", st);
-  k_gather_binned<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, idx, coords, f0, f1, f2); }
+  k_gather_binned<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, rec, f0, f1, f2); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
