@@ -229,7 +229,7 @@ int cola_status(cola_plan* plan, cola_stream stream);
  * Same result as cola_power on a plan with this ng and box: P(k) of the float32 density
  * delta [ng^3] in shells b = 1..nbins, written to the caller's device arrays k, pk (float64)
  * and nmodes (int64).  Its scratch is one static device array sized for ng <= 128 (about
- * 9.4 MiB held on every GPU that loads the library until the process exits); ng > 128 is
+ * 9.8 MiB held on every GPU that loads the library until the process exits); ng > 128 is
  * rejected with COLA_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture on the device.  Every call shares the one

@@ -453,6 +453,8 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     const Shape sh = box_shape(n, nt, e->tuning.tile_shape, e->tuning.radix);
     BoxDesc& d = e->h_boxes[b];
     d.g = p->geo;
+    if ((sh.ty & (sh.ty - 1)) || (sh.tz & (sh.tz - 1)))
+      return fail(COLA_EUNSUPPORTED, "ensemble: deposit tile sides must be powers of two");
     d.tl.ty = sh.ty;
     d.tl.tz = sh.tz;
     d.tl.nty = n / sh.ty;

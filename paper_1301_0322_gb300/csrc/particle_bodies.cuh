@@ -10,10 +10,11 @@ namespace cola {
 
 // key = ((tz_tile * nty) + ty_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
 // is the last row of its tile along y (z): its cloud also reaches the next tile.
+// Tile sizes are powers of two (4 x 2 rows for a plan, 2 .. 16 rows per axis in an ensemble).
 __device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
-  const int ty = cy / tl.ty, tz = cz / tl.tz;
-  const int ry = (cy - ty * tl.ty == tl.ty - 1) ? 1 : 0;
-  const int rz = (cz - tz * tl.tz == tl.tz - 1) ? 2 : 0;
+  const int ty = cy >> (__ffs(tl.ty) - 1), tz = cz >> (__ffs(tl.tz) - 1);
+  const int ry = ((cy & (tl.ty - 1)) == tl.ty - 1) ? 1 : 0;
+  const int rz = ((cz & (tl.tz - 1)) == tl.tz - 1) ? 2 : 0;
   return (tz * tl.nty + ty) * 4 + ry + rz;
 }
 

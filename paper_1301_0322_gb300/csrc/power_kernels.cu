@@ -7,6 +7,8 @@
 
 namespace cola {
 
+constexpr int kPowerChunks = 4;  // chunks of 32 modes whose loads a warp issues together
+
 __device__ __forceinline__ int shell_of(int m) {
   int r = (int)sqrtf((float)m);
   while ((r + 1) * (r + 1) <= m) ++r;
@@ -49,53 +51,70 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
     const int ky = (int)(row % ng), kz = (int)(row / ng);
     const int ny = ky < ng / 2 ? ky : ky - ng, nz = kz < ng / 2 ? kz : kz - ng;
     const int myz = ny * ny + nz * nz;
+    // shell b <= nbins iff |n|^2 <= nbins (nbins + 1): rows and chunks beyond that hold no mode
+    // of the requested shells and are skipped (warp-uniform)
+    const int lim = nbins * (nbins + 1) - myz;
+    if (lim < 0) continue;
     const float sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
     const float wyz = (sy * sy) * (sz * sz);
     const float row_scale = pnorm / (wyz * wyz);
     const float2* rowp = dk + row * P;
     const float2* rowq = NF == 2 ? dk2 + row * P : nullptr;
-    for (int c0 = 0; c0 < nh; c0 += 32) {
-      const int kx = c0 + lane;
-      int b = -1;
-      float q[NQ];
+    // chunks of 32 k_x in groups of kPowerChunks whose loads are all issued first
+    for (int g0 = 0; g0 < nh && g0 * g0 <= lim; g0 += 32 * kPowerChunks) {
+      float2 dv[kPowerChunks], ev[kPowerChunks];
 #pragma unroll
-      for (int j = 0; j < NQ; ++j) q[j] = 0.f;
-      if (kx < nh) {
-        const int m = kx * kx + myz;
-        const int sb = shell_of(m);
-        if (sb >= 1 && sb <= nbins) {
-          b = sb - 1;
-          const float w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
-          const float2 d = rowp[kx];
-          const float scale = w * (row_scale * inv_wx2[kx]);  // w P-normalisation / W(k)^2
-          q[0] = w * kf * sqrtf((float)m);
-          q[1] = (d.x * d.x + d.y * d.y) * scale;
-          if constexpr (NF == 2) {
-            const float2 e = rowq[kx];
-            q[2] = (e.x * e.x + e.y * e.y) * scale;
-            q[3] = (d.x * e.x + d.y * e.y) * scale;
+      for (int u = 0; u < kPowerChunks; ++u) {
+        const int kx = g0 + 32 * u + lane;
+        dv[u] = kx < nh ? rowp[kx] : make_float2(0.f, 0.f);
+        if constexpr (NF == 2) ev[u] = kx < nh ? rowq[kx] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kPowerChunks; ++u) {
+        const int c0 = g0 + 32 * u;
+        if (c0 >= nh || c0 * c0 > lim) break;  // warp-uniform
+        const int kx = c0 + lane;
+        int b = -1;
+        float q[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) q[j] = 0.f;
+        if (kx < nh) {
+          const int m = kx * kx + myz;
+          const int sb = shell_of(m);
+          if (sb >= 1 && sb <= nbins) {
+            b = sb - 1;
+            const float w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
+            const float2 d = dv[u];
+            const float scale = w * (row_scale * inv_wx2[kx]);  // w P-normalisation / W(k)^2
+            q[0] = w * kf * sqrtf((float)m);
+            q[1] = (d.x * d.x + d.y * d.y) * scale;
+            if constexpr (NF == 2) {
+              const float2 e = ev[u];
+              q[2] = (e.x * e.x + e.y * e.y) * scale;
+              q[3] = (d.x * e.x + d.y * e.y) * scale;
+            }
+            q[NQ - 1] = w;
           }
-          q[NQ - 1] = w;
         }
-      }
-      // segmented reduction toward the first lane of each run of equal shells
+        // segmented reduction toward the first lane of each run of equal shells
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int bo = __shfl_down_sync(0xffffffffu, b, o);
-        float qo[NQ];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int bo = __shfl_down_sync(0xffffffffu, b, o);
+          float qo[NQ];
 #pragma unroll
-        for (int j = 0; j < NQ; ++j) qo[j] = __shfl_down_sync(0xffffffffu, q[j], o);
-        if (lane + o < 32 && bo == b) {
+          for (int j = 0; j < NQ; ++j) qo[j] = __shfl_down_sync(0xffffffffu, q[j], o);
+          if (lane + o < 32 && bo == b) {
 #pragma unroll
-          for (int j = 0; j < NQ; ++j) q[j] += qo[j];
+            for (int j = 0; j < NQ; ++j) q[j] += qo[j];
+          }
         }
-      }
-      const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
-      if (b >= 0 && (lane == 0 || bprev != b)) {
+        const int bprev = __shfl_up_sync(0xffffffffu, b, 1);
+        if (b >= 0 && (lane == 0 || bprev != b)) {
 #pragma unroll
-        for (int j = 0; j < NQ; ++j) mine[NQ * b + j] += (double)q[j];
+          for (int j = 0; j < NQ; ++j) mine[NQ * b + j] += (double)q[j];
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   __syncthreads();

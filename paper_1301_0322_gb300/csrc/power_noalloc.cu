@@ -9,7 +9,7 @@
 //
 // The scratch (the half spectrum, the shell accumulators and the twiddle table) lives in the
 // file-scope device array below, sized for meshes up to COLA_NOALLOC_MAX_NG^3.  Every GPU that
-// loads this library keeps that array (about 9.4 MiB) until the process exits.  Host code must
+// loads this library keeps that array (about 9.8 MiB) until the process exits.  Host code must
 // not pass the array's name to a kernel: on the host that name is only a stand-in for the
 // device symbol, so its device address is looked up once per device with
 // cudaGetSymbolAddress and that address is what the kernels receive.
