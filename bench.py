@@ -603,17 +603,24 @@ def ensemble_timing(args, dev, rank, world):
         nm_ = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         kernels[nm_] = {"launches": int(launches[i]), "ms": float(msk[i])}
     peak, peak_kind = hbm_peak()
+    sized = ("keys", "scatter", "gather_kick_drift", "gather_binned", "kick_drift")
     for name, kv in kernels.items():
-        base = name[len("ens_"):]
         alg = 0
-        for n_p, ng, _ in boxes:
-            if base in ("keys", "scatter", "gather_kick_drift", "gather_binned", "kick_drift"):
-                a = algorithmic_bytes(base, n_p, ng)
-            elif base == "fft_y":
-                a = algorithmic_bytes(f"fft_cols_{ng}", n_p, ng)
-            else:
-                a = algorithmic_bytes(f"{base}_{ng}", n_p, ng)
-            alg = alg + a if a is not None and alg is not None else None
+        if name.startswith("ens_"):  # multi-box kernels: one launch covers every box
+            base = name[len("ens_"):]
+            for n_p, ng, _ in boxes:
+                if base in sized:
+                    a = algorithmic_bytes(base, n_p, ng)
+                elif base == "fft_y":
+                    a = algorithmic_bytes(f"fft_cols_{ng}", n_p, ng)
+                else:
+                    a = algorithmic_bytes(f"{base}_{ng}", n_p, ng)
+                alg = alg + a if a is not None and alg is not None else None
+        else:  # per-box launches: bytes of one box of the launch's size (mean over the boxes)
+            suffix = name.rsplit("_", 1)[-1]
+            of_size = [b for b in boxes if not suffix.isdigit() or b[1] == int(suffix)]
+            parts = [algorithmic_bytes(name, n_p, ng) for n_p, ng, _ in of_size]
+            alg = sum(parts) / len(parts) if parts and None not in parts else None
         avg = kv["ms"] / kv["launches"]
         kv["avg_launch_ms"] = avg
         if alg:
@@ -653,7 +660,7 @@ def ensemble_timing(args, dev, rank, world):
             "sequential_single_box": {"value": updates / (ms_seq * 1e-3), "ms_per_step": ms_seq},
             "speedup_vs_sequential": ms_seq / ms_ens,
             "tuning": {"threads": best.threads, "tile_shape": best.tile_shape, "blocks_per_sm": best.blocks_per_sm,
-                       "radix": best.radix},
+                       "radix": best.radix, "launch": best.launch},
             "tune_candidates_ms": [round(float(x), 4) for x in tune_ms],
             "step": "noise + 2LPT IC + 11 force evaluations (CUDA graph per step) + density + P(k), all boxes",
             "kernels": {k_: {kk_: (round(vv_, 5) if isinstance(vv_, float) else vv_) for kk_, vv_ in kv.items()}

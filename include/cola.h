@@ -259,7 +259,7 @@ int cola_power_noalloc(const float* delta, int32_t ng, double box, int32_t nbins
  * 256}; the total particle count below 2^31.  Other fields are free per box. */
 typedef struct cola_ensemble cola_ensemble;
 
-/* Tunable launch shape of the ensemble kernels (chosen by cola_ensemble_tune):
+/* Tunable launch shape of the ensemble step (chosen by cola_ensemble_tune):
  *  threads       block size of every persistent kernel, 128 or 256; it fixes the FFT
  *                columns per block (threads / (n / E)) and the deposit tile rows
  *  tile_shape    deposit tile (y x z rows) for a given row count: 0 = 4x2, 4x4, 8x4, 8x8,
@@ -271,15 +271,21 @@ typedef struct cola_ensemble cola_ensemble;
  *                (e.g. 256 = 16 x 16, 16 elements per thread), 1 = a second one with another
  *                number of elements per thread (256 = 8 x 8 x 4, 8 per thread).  Variant 0
  *                reproduces the single-box results bit for bit; variant 1 rounds differently
- *                (same transforms, another order of operations). */
+ *                (same transforms, another order of operations).
+ *  launch        0 = the multi-box persistent kernels above (one launch per kernel class and
+ *                force evaluation for all boxes); 1 = every box's own single-box launches
+ *                one box after another (threads, tile_shape, blocks_per_sm and radix are
+ *                then unused; the results equal the single-box ones bit for bit).  Either
+ *                way each step is replayed from a CUDA graph. */
 typedef struct {
   int32_t threads;
   int32_t tile_shape;
   int32_t blocks_per_sm;
   int32_t radix;
+  int32_t launch;
 } cola_ensemble_tuning;
 
-#define COLA_ENSEMBLE_TUNE_CANDIDATES 16
+#define COLA_ENSEMBLE_TUNE_CANDIDATES 17
 
 /* Create / destroy.  boxes: host array of nbox configurations (see the requirements above). */
 int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out);
@@ -312,13 +318,14 @@ int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola
 int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
                         int64_t* nmodes, cola_stream stream);
 /* Autotuner: times one force evaluation without the particle update (binning, mesh passes and
- * the gather into scratch) at displacements s (read only) for each of the
+ * the gather into scratch) of all boxes at displacements s (read only) for each of the
  * COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
  * repetitions after one warm-up, CUDA events on `stream`; synchronises), keeps the fastest
  * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
- * milliseconds of each candidate, in the order threads in {128, 256} x tile_shape in {0, 1}
- * x blocks_per_sm in {0, 2} x radix in {0, 1} (radix fastest).  Candidates with the same
- * radix give bit-identical results. */
+ * milliseconds of each candidate: first the 16 multi-box shapes (launch 0) in the order
+ * threads in {128, 256} x tile_shape in {0, 1} x blocks_per_sm in {0, 2} x radix in {0, 1}
+ * (radix fastest), then launch 1.  Candidates with radix 0 (and launch 1) give results
+ * bit-identical to the single-box runs. */
 int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
                        cola_stream stream);
 int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning);

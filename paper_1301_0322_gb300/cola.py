@@ -47,7 +47,7 @@ SCHEMES = {"cola": 0, "cola_std": 1, "pm_std": 2, "cola_u1": 3}
 
 class cola_ensemble_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("radix", ctypes.c_int32)]
+                ("radix", ctypes.c_int32), ("launch", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -94,7 +94,7 @@ _SIGNATURES = {
     "cola_ensemble_profile": [_P, ctypes.c_int32],
     "cola_ensemble_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
 }
-COLA_ENSEMBLE_TUNE_CANDIDATES = 16
+COLA_ENSEMBLE_TUNE_CANDIDATES = 17
 _lib = None
 
 
@@ -542,11 +542,11 @@ class Ensemble:
     @property
     def tuning(self):
         t = cola_ensemble_get_tuning(self.handle)
-        return (t.threads, t.tile_shape, t.blocks_per_sm, t.radix)
+        return (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch)
 
     @tuning.setter
     def tuning(self, value):
-        value = tuple(value) + (0,) * (4 - len(value))
+        value = tuple(value) + (0,) * (5 - len(value))
         cola_ensemble_set_tuning(self.handle, cola_ensemble_tuning(*value))
 
     def use_graphs(self, enable):

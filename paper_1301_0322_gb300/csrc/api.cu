@@ -89,6 +89,14 @@ static int force_meshes(cola_plan* p, const float* s, cudaStream_t st) {
                              p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
 }
 
+int plan_force_scratch(cola_plan* p, const float* s, cudaStream_t st) {
+  int rc = force_meshes(p, s, st);
+  if (rc || !p->binned_gather) return rc;
+  Workspace& w = p->ws;
+  return launch_gather_binned(p->geo, w.freal, w.rec, reinterpret_cast<float*>(w.meshA),
+                              reinterpret_cast<float*>(w.meshG[1]), reinterpret_cast<float*>(w.meshG[2]), st);
+}
+
 }  // namespace cola
 
 namespace cola {

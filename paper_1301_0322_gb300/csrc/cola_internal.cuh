@@ -140,6 +140,10 @@ int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, fl
                              const float* s2, const float* coef_row, int mode, float* gout, cudaStream_t st);
 // the gather in bin order of the last binning (records rec) into fj[p], and the kick/drift in
 // lattice order from those forces
+// one force evaluation of a plan without the particle update (binning, mesh passes, and the
+// gather into the free half-spectrum buffers when the plan gathers in bin order): what the
+// ensemble autotuner times for the per-box launch mode
+int plan_force_scratch(cola_plan* p, const float* s, cudaStream_t st);
 int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec,
                          float* f0, float* f1, float* f2, cudaStream_t st);
 int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,

@@ -375,7 +375,7 @@ struct cola_ensemble {
   BoxDesc* d_boxes = nullptr;
   int* d_starts = nullptr;
   // current launch configuration
-  cola_ensemble_tuning tuning{256, 0, 0, 0};
+  cola_ensemble_tuning tuning{256, 0, 0, 0, 0};
   std::vector<BoxDesc> h_boxes;
   std::vector<int> h_starts;
   int total_bins = 0;
@@ -628,8 +628,8 @@ int check_ens(const cola_ensemble* e) {
 
 bool valid_tuning(const cola_ensemble_tuning& t) {
   return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) &&
-         (t.radix == 0 || t.radix == 1) && t.blocks_per_sm >= 0 &&
-         t.blocks_per_sm <= 64;
+         (t.radix == 0 || t.radix == 1) && t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64 &&
+         (t.launch == 0 || t.launch == 1);
 }
 
 // Run `enqueue` on `st`: directly (graphs off or profiling), or as a CUDA graph recorded on
@@ -856,7 +856,16 @@ int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, con
   if (!s || !v || !s1 || !s2) return fail(COLA_EINVAL, "null array");
   if (step < 0 || step > ens->nsteps) return fail(COLA_EINVAL, "step out of range");
   return replay(ens, ens->graphs[step], {u(s), u(v), u(s1), u(s2)},
-                [&](cudaStream_t st) { return enqueue_step_any(ens, step, s, v, s1, s2, st); },
+                [&](cudaStream_t st) {
+                  if (ens->tuning.launch == 0) return enqueue_step_any(ens, step, s, v, s1, s2, st);
+                  // launch mode 1: every box's single-box step, one box after another
+                  for (int b = 0; b < ens->nbox; ++b) {
+                    const int64_t o3 = 3 * ens->poff[b];
+                    const int rc = cola_step(ens->plans[b], step, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)st);
+                    if (rc) return rc;
+                  }
+                  return (int)COLA_OK;
+                },
                 (cudaStream_t)stream);
 }
 
@@ -897,7 +906,7 @@ int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tun
 int cola_ensemble_set_tuning(cola_ensemble* ens, const cola_ensemble_tuning* tuning, cola_stream stream) {
   int rc = check_ens(ens);
   if (rc) return rc;
-  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape 0 or 1");
+  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape, radix and launch 0 or 1, blocks_per_sm 0..64");
   const cola_ensemble_tuning old = ens->tuning;
   ens->tuning = *tuning;
   if ((rc = configure(ens, (cudaStream_t)stream))) {
@@ -922,15 +931,25 @@ int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_en
   cola_ensemble_tuning winner = start;
   double best_ms = 1e300;
   ProfilerGuard pg(nullptr);
+  // one force evaluation of all boxes without the particle update, in the candidate's mode
+  auto force = [&]() -> int {
+    if (ens->tuning.launch == 0) return enqueue_force_any(ens, s, st);
+    for (int b = 0; b < ens->nbox; ++b) {
+      const int r = plan_force_scratch(ens->plans[b], s + 3 * ens->poff[b], st);
+      if (r) return r;
+    }
+    return COLA_OK;
+  };
   for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
-    ens->tuning = cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1};
+    ens->tuning = i < 16 ? cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1, 0}
+                         : cola_ensemble_tuning{128, 0, 0, 0, 1};
     if ((rc = configure(ens, st))) break;
-    if ((rc = enqueue_force_any(ens, s, st))) break;  // warm-up
+    if ((rc = force())) break;  // warm-up
     if (cudaEventRecord(e0, st) != cudaSuccess) {
       rc = fail(COLA_ECUDA, "event record");
       break;
     }
-    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_force_any(ens, s, st);
+    for (int r = 0; r < reps && !rc; ++r) rc = force();
     if (rc) break;
     float el = 0.f;
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

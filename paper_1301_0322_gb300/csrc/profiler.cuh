@@ -68,9 +68,12 @@ class LaunchScope {
   bool active_ = false;
 };
 
-// Sets the profiler of the plan used by the current API call.
+// Sets the profiler of the plan used by the current API call.  A call made inside another call
+// that is profiling (an ensemble running its boxes' plans) records into that outer profiler.
 struct ProfilerGuard {
-  explicit ProfilerGuard(Profiler* p) : prev_(t_profiler) { t_profiler = p; }
+  explicit ProfilerGuard(Profiler* p) : prev_(t_profiler) {
+    if (!(prev_ && prev_->on)) t_profiler = p;
+  }
   ~ProfilerGuard() { t_profiler = prev_; }
   Profiler* prev_;
 };

@@ -6,8 +6,9 @@ code as the single-box kernels, only grouped differently into blocks and launche
 deposit sums are integers (order-independent).  So each box's result must equal the
 single-box result bit for bit -- and the single-box path is the one checked against the
 float64 oracle in test_gpu_parity.py.  The same holds for every launch shape the autotuner
-may pick with the single-box FFT factorisation (radix variant 0) and for graph replay versus
-direct launches; the second factorisation (variant 1) agrees to float32 rounding.
+may pick with the single-box FFT factorisation (radix variant 0), for the per-box launch mode
+(each box's single-box launches in the step graph) and for graph replay versus direct
+launches; the second factorisation (variant 1) agrees to float32 rounding.
 """
 import numpy as np
 import pytest
@@ -92,7 +93,7 @@ def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, bloc
     ens.tuning = (256, 0, 0, 0)
     ref_s, ref_v = run_steps(ens, SEEDS, 2)
     ens.tuning = (threads, tile_shape, blocks_per_sm, radix)
-    assert ens.tuning == (threads, tile_shape, blocks_per_sm, radix)
+    assert ens.tuning == (threads, tile_shape, blocks_per_sm, radix, 0)
     s, v = run_steps(ens, SEEDS, 2)
     ens.status()
     if radix == 0:
@@ -103,6 +104,20 @@ def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, bloc
             vb, rvb = ens.split(v)[b], ens.split(ref_v)[b]
             assert float((sb - rb).abs().max()) <= 5e-4 * box / ng, b
             assert float((vb - rvb).abs().max()) <= 5e-4 * float(rvb.pow(2).mean().sqrt()), b
+
+
+def test_per_box_launch_mode_gives_the_same_result(ens):
+    ens.tuning = (256, 0, 0, 0)
+    ref_s, ref_v = run_steps(ens, SEEDS, 2)
+    ens.tuning = (128, 0, 0, 0, 1)
+    assert ens.tuning == (128, 0, 0, 0, 1)
+    for graphs in (True, False):
+        ens.use_graphs(graphs)
+        s, v = run_steps(ens, SEEDS, 2)
+        ens.status()
+        assert torch.equal(s, ref_s) and torch.equal(v, ref_v)
+    ens.use_graphs(True)
+    ens.tuning = (256, 0, 0, 0)
 
 
 def test_graph_replay_equals_direct_launches(cola, ens):
@@ -117,7 +132,11 @@ def test_graph_replay_equals_direct_launches(cola, ens):
     assert torch.equal(s_g2, s_e) and torch.equal(v_g2, v_e)
 
 
-def test_graph_replay_launches_twelve_kernels_per_step(cola, ens):
+@pytest.mark.parametrize("launch,per_step", [(0, 12), (1, 12 * len(BOXES))])
+def test_graph_replay_launch_count_per_step(cola, ens, launch, per_step):
+    # keys, three scan passes, scatter, deposit + x r2c, forward y, z + Green, inverse y,
+    # inverse x, gather in bin order, kick/drift: once for all boxes (launch 0) or per box (1)
+    ens.tuning = (256, 0, 0, 0, launch)
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     ens.step(0, s, v, s1, s2)  # records the graph for these pointers
     torch.cuda.synchronize()
@@ -127,17 +146,17 @@ def test_graph_replay_launches_twelve_kernels_per_step(cola, ens):
     lib.cola_launch_count(ctypes.byref(c0))
     ens.step(0, s, v, s1, s2)
     lib.cola_launch_count(ctypes.byref(c1))
-    # keys, three scan passes, scatter, deposit + x r2c, forward y, z + Green, inverse y,
-    # inverse x, gather in bin order, kick/drift
-    assert c1.value - c0.value == 12
+    assert c1.value - c0.value == per_step
+    ens.tuning = (256, 0, 0, 0)
 
 
 def test_autotuner_picks_the_fastest_candidate(cola, ens):
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     best, ms = ens.tune(s, reps=2)
-    assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix) == ens.tuning
-    assert np.all(ms > 0) and len(ms) == 16
-    order = [(t, sh, b, r) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
+    assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix, best.launch) == ens.tuning
+    assert np.all(ms > 0) and len(ms) == 17
+    order = [(t, sh, b, r, 0) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
+    order.append((128, 0, 0, 0, 1))
     assert order[int(np.argmin(ms))] == ens.tuning
     ens.status()
 
