@@ -273,10 +273,11 @@ typedef struct cola_ensemble cola_ensemble;
  *                reproduces the single-box results bit for bit; variant 1 rounds differently
  *                (same transforms, another order of operations).
  *  launch        0 = the multi-box persistent kernels above (one launch per kernel class and
- *                force evaluation for all boxes); 1 = every box's own single-box launches
- *                one box after another (threads, tile_shape, blocks_per_sm and radix are
- *                then unused; the results equal the single-box ones bit for bit).  Either
- *                way each step is replayed from a CUDA graph. */
+ *                force evaluation for all boxes); 1, 2 or 4 = every box's own single-box
+ *                launches, the boxes dealt round-robin over that many streams forked inside
+ *                the step graph, one box after another on each (threads, tile_shape,
+ *                blocks_per_sm and radix are then unused; the results equal the single-box
+ *                ones bit for bit).  Either way each step is replayed from a CUDA graph. */
 typedef struct {
   int32_t threads;
   int32_t tile_shape;
@@ -285,7 +286,7 @@ typedef struct {
   int32_t launch;
 } cola_ensemble_tuning;
 
-#define COLA_ENSEMBLE_TUNE_CANDIDATES 17
+#define COLA_ENSEMBLE_TUNE_CANDIDATES 19
 
 /* Create / destroy.  boxes: host array of nbox configurations (see the requirements above). */
 int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out);
@@ -324,8 +325,8 @@ int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, d
  * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
  * milliseconds of each candidate: first the 16 multi-box shapes (launch 0) in the order
  * threads in {128, 256} x tile_shape in {0, 1} x blocks_per_sm in {0, 2} x radix in {0, 1}
- * (radix fastest), then launch 1.  Candidates with radix 0 (and launch 1) give results
- * bit-identical to the single-box runs. */
+ * (radix fastest), then launch 1, 2 and 4.  Candidates with radix 0 and the per-box ones give
+ * results bit-identical to the single-box runs. */
 int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
                        cola_stream stream);
 int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning);

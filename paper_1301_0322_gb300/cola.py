@@ -94,7 +94,7 @@ _SIGNATURES = {
     "cola_ensemble_profile": [_P, ctypes.c_int32],
     "cola_ensemble_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
 }
-COLA_ENSEMBLE_TUNE_CANDIDATES = 17
+COLA_ENSEMBLE_TUNE_CANDIDATES = 19
 _lib = None
 
 

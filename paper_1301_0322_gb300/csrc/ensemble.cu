@@ -629,7 +629,7 @@ int check_ens(const cola_ensemble* e) {
 bool valid_tuning(const cola_ensemble_tuning& t) {
   return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) &&
          (t.radix == 0 || t.radix == 1) && t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64 &&
-         (t.launch == 0 || t.launch == 1);
+         (t.launch == 0 || t.launch == 1 || t.launch == 2 || t.launch == 4);
 }
 
 // Run `enqueue` on `st`: directly (graphs off or profiling), or as a CUDA graph recorded on
@@ -679,8 +679,7 @@ uintptr_t u(const void* p) { return reinterpret_cast<uintptr_t>(p); }
 // and joined back into `st` (inside a capture the forks become parallel graph branches; the
 // boxes use disjoint workspaces, so their work is independent).
 template <class F>
-int fork_join(cola_ensemble* e, cudaStream_t st, F&& per_box) {
-  constexpr int K = cola_ensemble::kForks;
+int fork_join(cola_ensemble* e, cudaStream_t st, F&& per_box, int K = cola_ensemble::kForks) {
   COLA_CUDA_CHECK(cudaEventRecord(e->fork_ev, st));
   for (int k = 0; k < K; ++k) COLA_CUDA_CHECK(cudaStreamWaitEvent(e->side[k], e->fork_ev, 0));
   int rc = COLA_OK;
@@ -858,12 +857,15 @@ int cola_ensemble_step(cola_ensemble* ens, int32_t step, float* s, float* v, con
   return replay(ens, ens->graphs[step], {u(s), u(v), u(s1), u(s2)},
                 [&](cudaStream_t st) {
                   if (ens->tuning.launch == 0) return enqueue_step_any(ens, step, s, v, s1, s2, st);
-                  // launch mode 1: every box's single-box step, one box after another
-                  for (int b = 0; b < ens->nbox; ++b) {
+                  // per-box launch modes: every box's single-box step, the boxes dealt over
+                  // `launch` streams (one box after another on each)
+                  auto box_step = [&](int b, cudaStream_t sb) {
                     const int64_t o3 = 3 * ens->poff[b];
-                    const int rc = cola_step(ens->plans[b], step, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)st);
-                    if (rc) return rc;
-                  }
+                    return cola_step(ens->plans[b], step, s + o3, v + o3, s1 + o3, s2 + o3, (cola_stream)sb);
+                  };
+                  if (ens->tuning.launch > 1) return fork_join(ens, st, box_step, ens->tuning.launch);
+                  for (int b = 0; b < ens->nbox; ++b)
+                    if (const int rc = box_step(b, st)) return rc;
                   return (int)COLA_OK;
                 },
                 (cudaStream_t)stream);
@@ -906,7 +908,7 @@ int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tun
 int cola_ensemble_set_tuning(cola_ensemble* ens, const cola_ensemble_tuning* tuning, cola_stream stream) {
   int rc = check_ens(ens);
   if (rc) return rc;
-  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape, radix and launch 0 or 1, blocks_per_sm 0..64");
+  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape and radix 0 or 1, blocks_per_sm 0..64, launch 0, 1, 2 or 4");
   const cola_ensemble_tuning old = ens->tuning;
   ens->tuning = *tuning;
   if ((rc = configure(ens, (cudaStream_t)stream))) {
@@ -934,15 +936,15 @@ int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_en
   // one force evaluation of all boxes without the particle update, in the candidate's mode
   auto force = [&]() -> int {
     if (ens->tuning.launch == 0) return enqueue_force_any(ens, s, st);
-    for (int b = 0; b < ens->nbox; ++b) {
-      const int r = plan_force_scratch(ens->plans[b], s + 3 * ens->poff[b], st);
-      if (r) return r;
-    }
+    auto box_force = [&](int b, cudaStream_t sb) { return plan_force_scratch(ens->plans[b], s + 3 * ens->poff[b], sb); };
+    if (ens->tuning.launch > 1) return fork_join(ens, st, box_force, ens->tuning.launch);
+    for (int b = 0; b < ens->nbox; ++b)
+      if (const int r = box_force(b, st)) return r;
     return COLA_OK;
   };
   for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
     ens->tuning = i < 16 ? cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1, 0}
-                         : cola_ensemble_tuning{128, 0, 0, 0, 1};
+                         : cola_ensemble_tuning{128, 0, 0, 0, 1 << (i - 16)};
     if ((rc = configure(ens, st))) break;
     if ((rc = force())) break;  // warm-up
     if (cudaEventRecord(e0, st) != cudaSuccess) {

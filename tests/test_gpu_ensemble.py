@@ -106,11 +106,12 @@ def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, bloc
             assert float((vb - rvb).abs().max()) <= 5e-4 * float(rvb.pow(2).mean().sqrt()), b
 
 
-def test_per_box_launch_mode_gives_the_same_result(ens):
+@pytest.mark.parametrize("streams", [1, 2, 4])
+def test_per_box_launch_mode_gives_the_same_result(ens, streams):
     ens.tuning = (256, 0, 0, 0)
     ref_s, ref_v = run_steps(ens, SEEDS, 2)
-    ens.tuning = (128, 0, 0, 0, 1)
-    assert ens.tuning == (128, 0, 0, 0, 1)
+    ens.tuning = (128, 0, 0, 0, streams)
+    assert ens.tuning == (128, 0, 0, 0, streams)
     for graphs in (True, False):
         ens.use_graphs(graphs)
         s, v = run_steps(ens, SEEDS, 2)
@@ -132,7 +133,7 @@ def test_graph_replay_equals_direct_launches(cola, ens):
     assert torch.equal(s_g2, s_e) and torch.equal(v_g2, v_e)
 
 
-@pytest.mark.parametrize("launch,per_step", [(0, 12), (1, 12 * len(BOXES))])
+@pytest.mark.parametrize("launch,per_step", [(0, 12), (1, 12 * len(BOXES)), (2, 12 * len(BOXES))])
 def test_graph_replay_launch_count_per_step(cola, ens, launch, per_step):
     # keys, three scan passes, scatter, deposit + x r2c, forward y, z + Green, inverse y,
     # inverse x, gather in bin order, kick/drift: once for all boxes (launch 0) or per box (1)
@@ -154,9 +155,9 @@ def test_autotuner_picks_the_fastest_candidate(cola, ens):
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     best, ms = ens.tune(s, reps=2)
     assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix, best.launch) == ens.tuning
-    assert np.all(ms > 0) and len(ms) == 17
+    assert np.all(ms > 0) and len(ms) == 19
     order = [(t, sh, b, r, 0) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
-    order.append((128, 0, 0, 0, 1))
+    order += [(128, 0, 0, 0, 1), (128, 0, 0, 0, 2), (128, 0, 0, 0, 4)]
     assert order[int(np.argmin(ms))] == ens.tuning
     ens.status()
 
