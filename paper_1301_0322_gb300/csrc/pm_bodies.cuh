@@ -62,8 +62,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   const int y0 = tyi * TY, z0 = tzi * TZ;
   for (int i = threadIdx.x; i < ROWS * N; i += NT) acc[i] = 0ull;
   // the tile's own 4 bins and the boundary bins of its 3 lower neighbours, loaded in parallel
-  if (threadIdx.x < 9) {
-    const int k = threadIdx.x;
+  // (a loop: at N = 32 and 48 a block has only 8 threads)
+  for (int k = threadIdx.x; k < 9; k += NT) {
     const int tym = tyi == 0 ? tl.nty - 1 : tyi - 1;
     const int tzm = tzi == 0 ? tl.ntz - 1 : tzi - 1;
     const int ty_ = (k == 4 || k == 5 || k == 8) ? tym : tyi;

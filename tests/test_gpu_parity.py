@@ -111,7 +111,10 @@ def test_deposit_bit_exact(cola, case):
     plan.status()
 
 
-@pytest.mark.parametrize("n_p,ng,deconv", [(32, 64, 1), (32, 64, 0), (32, 96, 2), (48, 96, 1)])
+# the smallest meshes (32, 48: 8-thread deposit blocks), a lattice as fine as the mesh and one
+# finer than it
+@pytest.mark.parametrize("n_p,ng,deconv", [(32, 64, 1), (32, 64, 0), (32, 96, 2), (48, 96, 1), (32, 48, 1),
+                                           (32, 32, 1), (48, 32, 1), (48, 48, 0)])
 def test_unit_force_matches_oracle(cola, n_p, ng, deconv):
     box = 100.0
     plan = cola.Plan(np_side=n_p, ng=ng, box=box, deconv=deconv)
@@ -291,3 +294,29 @@ def test_runs_match_the_quantised_oracle(cola, nsteps):
           f"{np.abs(ref_q['s'] - ref['s']).max() / cell:.2e} cell")
     assert ds_q <= 1e-3
     assert dv_q <= 1e-3
+
+
+def test_mesh_coarser_than_the_lattice_gathers_in_lattice_order(cola):
+    # 48^3 particles on a 32^3 mesh: a half spectrum (32^2 x 20 complex) cannot hold one force
+    # component per particle, so the step gathers in lattice order (k_gather_kick_drift)
+    # instead of in bin order; the run must still follow the quantised oracle (also a
+    # lattice that is not an integer multiple of the mesh: fixed-point origin by division)
+    import ctypes
+    n_p, ng, box, nsteps = 48, 32, 100.0, 3
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=nsteps)
+    lib = cola.load_library()
+    lib.cola_profile(plan.handle, 1)
+    w = inputs.gaussian_noise(n_p, 2)
+    s, v = gpu_run(cola, plan, w)
+    lib.cola_profile(plan.handle, 0)
+    names = ctypes.create_string_buffer(64 * 64)
+    launches, ms, count = (ctypes.c_int64 * 64)(), (ctypes.c_double * 64)(), ctypes.c_int32()
+    lib.cola_profile_read(plan.handle, 64, names, launches, ms, ctypes.byref(count))
+    kernels = {names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode() for i in range(count.value)}
+    assert "gather_kick_drift" in kernels and "gather_binned" not in kernels
+    w64 = w.reshape(n_p, n_p, n_p).astype(np.float64)
+    ref_q = ocola.run(w64, ocola.ColaConfig(n_p=n_p, n_g=ng, box=box, nsteps=nsteps, fixed_bits=16))
+    cell = box / ng
+    sg, vg = host(s), host(v)
+    assert np.abs(sg - ref_q["s"]).max() / cell <= 1e-3
+    assert np.abs(vg - ref_q["v"]).max() / np.sqrt(np.mean(ref_q["v"] ** 2)) <= 1e-3
