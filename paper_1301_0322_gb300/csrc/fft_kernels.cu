@@ -9,13 +9,6 @@
 
 namespace cola {
 
-// columns per block of the strided passes (16 columns = 128 contiguous bytes per row); blocks
-// of at most 256 threads (512 for the longest transforms) so that two blocks fit on an SM with
-// every thread's E elements in registers, and one block's loads overlap the other's FFT
-template <int N>
-__host__ __device__ constexpr int col_width() {
-  return FFTConf<N>::T * 16 <= 256 ? 16 : (FFTConf<N>::T * 8 <= 256 ? 8 : (FFTConf<N>::T * 4 <= 512 ? 4 : 2));
-}
 // rows per block of the contiguous x passes (about 256 threads per block)
 template <int N>
 __host__ __device__ constexpr int x_rows() {

@@ -21,9 +21,11 @@ __device__ __forceinline__ int signed_mode(int k, int n) { return k < n / 2 ? k 
 // first-derivative factor i k_j (zero on the Nyquist plane |n_j| = N/2)
 __device__ __forceinline__ float2 mul_ik(float2 a, float k) { return make_float2(__fmul_rn(-k, a.y), __fmul_rn(k, a.x)); }
 
-
+// columns per block of the strided passes (16 columns = 128 contiguous bytes per row); blocks
+// of at most 256 threads (512 for the longest transforms) so that two blocks fit on an SM with
+// every thread's E elements in registers, and one block's loads overlap the other's FFT
 template <int N>
-__host__ __device__ constexpr int green_width() {
+__host__ __device__ constexpr int col_width() {
   return FFTConf<N>::T * 16 <= 256 ? 16 : (FFTConf<N>::T * 8 <= 256 ? 8 : (FFTConf<N>::T * 4 <= 512 ? 4 : 2));
 }
 

@@ -27,19 +27,19 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, (512 / (FFTConf<N
 }
 
 template <int N>
-__global__ void __launch_bounds__(FFTConf<N>::T * green_width<N>(), 2)
+__global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
     k_fft_z_green(float2* __restrict__ A, float2* __restrict__ Gz, int P, float kf, int deconv, float norm,
                   const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
-  z_green_body<N, green_width<N>()>(A, Gz, P, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
+  z_green_body<N, col_width<N>()>(A, Gz, P, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int N>
-__global__ void __launch_bounds__(FFTConf<N>::T * green_width<N>(), 2)
+__global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
     k_fft_y_inv3(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz, int P, float kf,
                  const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
-  y_inv3_body<N, green_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
+  y_inv3_body<N, col_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
 // Persistent: each block walks items blockIdx.x, blockIdx.x + gridDim.x, ... with the bulk
@@ -104,7 +104,7 @@ template <int N>
 static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                           float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv,
                           const float2* tw, int* err, cudaStream_t st) {
-  constexpr int M = N / 2, W = green_width<N>(), nh = N / 2 + 1;
+  constexpr int M = N / 2, W = col_width<N>(), nh = N / 2 + 1;
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const float norm = (float)(1.0 / ((double)N * N * N));
   int rc;
@@ -157,17 +157,20 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     const int64_t nrows = (int64_t)N * N;
     if (nrows % RB) return fail(COLA_EINVAL, "fused c2r: row count not a multiple of the block rows");
     if (P % 4) return fail(COLA_EINVAL, "fused c2r: row pitch must be a multiple of 4 complex");
-    static int grid_cap = 0;
-    if (!grid_cap) {
-      int occ = 0, dev = 0, sms = 0;
+    // resident blocks x SMs of the current device (cached per device)
+    static int grid_cap[64] = {};
+    int dev = 0;
+    COLA_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(COLA_EUNSUPPORTED, "device index above 63");
+    if (!grid_cap[dev]) {
+      int occ = 0, sms = 0;
       COLA_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_x_c2r3<N>, T * RB, smem));
-      COLA_CUDA_CHECK(cudaGetDevice(&dev));
       COLA_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       if (occ < 1) return fail(COLA_EUNSUPPORTED, "fused c2r does not fit on an SM");
-      grid_cap = occ * sms;
+      grid_cap[dev] = occ * sms;
     }
     const int64_t items = 3 * nrows / RB;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, grid_cap);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, grid_cap[dev]);
     LaunchScope ls_(flabel<N>(3), st);
     k_fft_x_c2r3<N><<<grid, T * RB, smem, st>>>(A, Gy, Gz, F, P, kf, tw, err);
     COLA_LAUNCH_CHECK();
