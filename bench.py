@@ -370,7 +370,7 @@ def gb300_arm(args):
         e_noise = [plan._empty(n3), plan._empty(n3)]
         e_delta = plan._empty(ng**3)
         copy_stream = torch.cuda.Stream(device=dev)
-        ev_ic, ev_steps, ev_noise, ev_state = (torch.cuda.Event() for _ in range(4))
+        ev_ic, ev_s, ev_steps, ev_noise, ev_state = (torch.cuda.Event() for _ in range(5))
         e_noise[0].copy_(h_noise)
         torch.cuda.synchronize()
         ke = max(1, min(args.steps, 5))
@@ -388,10 +388,14 @@ def gb300_arm(args):
                 ev_noise.record(copy_stream)
             for i in range(NSTEPS + 1):
                 cola.cola_step(h, i, s, v, s1, s2)
+                if i == NSTEPS - 1:  # s is final here (the last evaluation kicks v only): copy it out
+                    ev_s.record(stream)
+                    with torch.cuda.stream(copy_stream):
+                        copy_stream.wait_event(ev_s)
+                        h_s.copy_(s, non_blocking=True)
             ev_steps.record(stream)
-            with torch.cuda.stream(copy_stream):  # the final state, device -> host
+            with torch.cuda.stream(copy_stream):  # the final v, device -> host
                 copy_stream.wait_event(ev_steps)
-                h_s.copy_(s, non_blocking=True)
                 h_v.copy_(v, non_blocking=True)
                 ev_state.record(copy_stream)
             cola.cola_density(h, s, None, e_delta)
