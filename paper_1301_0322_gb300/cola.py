@@ -450,8 +450,10 @@ def _make_config(np_side, ng, box, omega_m=0.27, omega_l=0.73, h=0.7, sigma8=0.8
 
 
 class Ensemble:
-    """Independent COLA boxes of different sizes evolved together (one launch per kernel class
-    per force evaluation, each step replayed from a CUDA graph).
+    """Independent COLA boxes of different sizes evolved together, each step replayed from a
+    CUDA graph: either one multi-box launch per kernel class and force evaluation, or every
+    box's own single-box launches dealt over 1, 2 or 4 forked streams (``tuning``; ``tune``
+    times all candidates and keeps the fastest).
 
     ``boxes``: sequence of (np_side, ng, box) tuples or dicts of Plan keyword arguments.
     Particle arrays are concatenated over boxes: a [3, n_total] tensor holds box b's SoA block
@@ -536,11 +538,15 @@ class Ensemble:
         return k, pk, nm
 
     def tune(self, s, reps=3):
+        """Times the COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes at displacements s (read only),
+        keeps the fastest; returns (best tuning struct, per-candidate milliseconds)."""
         _expect(s, torch.float32, 3 * self.n_total, "s")
         return cola_ensemble_tune(self.handle, s, reps)
 
     @property
     def tuning(self):
+        """(threads, tile_shape, blocks_per_sm, radix, launch); a shorter tuple given to the
+        setter is padded with zeros (launch 0 = the multi-box kernels)."""
         t = cola_ensemble_get_tuning(self.handle)
         return (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch)
 
