@@ -152,6 +152,62 @@ def test_bbks_limits(lcdm):
     assert float(lcdm.transfer_bbks(k)) == pytest.approx(asym, rel=1e-5)
 
 
+def _bbks_of_q(lcdm, q):
+    return np.asarray(lcdm.transfer_bbks(np.asarray(q, dtype=np.float64) * lcdm.omega_m * lcdm.h))
+
+
+def test_bbks_small_q_taylor_coefficients(lcdm):
+    # The limits above fix only 2.34 and 6.71.  The interior coefficients of the BBKS fit
+    # (Bardeen, Bond, Kaiser & Szalay 1986, eq. G3), T = ln(1 + 2.34 q)/(2.34 q) (1 + u)^(-1/4)
+    # with u = 3.89 q + (16.1 q)^2 + (5.46 q)^3 + (6.71 q)^4, enter the Taylor series at q = 0:
+    #   ln(1 + x)/x = 1 - x/2 + x^2/3 - ...,   (1 + u)^(-1/4) = 1 - u/4 + (5/32) u^2 - ...
+    # so T = 1 + c1 q + c2 q^2 + O(q^3) with
+    #   c1 = -2.34/2 - 3.89/4
+    #   c2 = 2.34^2/3 + (2.34/2)(3.89/4) - 16.1^2/4 + (5/32) 3.89^2
+    # c1 pins 3.89 and c2 pins 16.1.  The coefficients are read off the oracle by a least
+    # squares fit of (T - 1)/q on q in [1e-5, 2e-3] (a quartic, so that the higher orders do
+    # not leak into c1, c2).
+    c1 = -2.34 / 2.0 - 3.89 / 4.0
+    c2 = 2.34**2 / 3.0 + (2.34 / 2.0) * (3.89 / 4.0) - 16.1**2 / 4.0 + 5.0 / 32.0 * 3.89**2
+    q = np.linspace(1e-5, 2e-3, 400)
+    y = (_bbks_of_q(lcdm, q) - 1.0) / q
+    fit = np.polynomial.polynomial.polyfit(q, y, 4)
+    assert fit[0] == pytest.approx(c1, rel=1e-7)
+    assert fit[1] == pytest.approx(c2, rel=1e-4)
+
+
+def test_bbks_large_q_correction(lcdm):
+    # For q -> oo, T (6.71 q) (2.34 q) / ln(1 + 2.34 q) = (1 + u / (6.71 q)^4)^(-1/4)
+    #   = 1 - 5.46^3 / (4 * 6.71^4 q) + O(q^-2):  the 1/q term pins 5.46 (given 6.71).
+    expect = -(5.46**3) / (4.0 * 6.71**4)
+    for q in (1e5, 1e6):
+        x = 2.34 * q
+        r = float(_bbks_of_q(lcdm, q)) * 6.71 * q * x / math.log1p(x)
+        assert (r - 1.0) * q == pytest.approx(expect, rel=2e-3)
+
+
+def test_bbks_interior_values_and_ratio(lcdm):
+    # An independent transcription of eq. G3 of BBKS, term by term in plain floats, at
+    # q = 0.1, 1 and 10, and the ratio T(0.3)/T(3), which weighs the 3.89 and 16.1 terms
+    # against the 5.46 and 6.71 terms.
+    def t_bbks(q):
+        lead = math.log(1.0 + 2.34 * q) / (2.34 * q)
+        s = 1.0
+        s += 3.89 * q
+        s += (16.1 * q) * (16.1 * q)
+        s += (5.46 * q) * (5.46 * q) * (5.46 * q)
+        s += (6.71 * q) * (6.71 * q) * (6.71 * q) * (6.71 * q)
+        return lead / math.sqrt(math.sqrt(s))
+
+    for q in (0.1, 1.0, 10.0):
+        assert float(_bbks_of_q(lcdm, q)) == pytest.approx(t_bbks(q), rel=1e-13)
+    ratio = float(_bbks_of_q(lcdm, 0.3)) / float(_bbks_of_q(lcdm, 3.0))
+    assert ratio == pytest.approx(t_bbks(0.3) / t_bbks(3.0), rel=1e-13)
+    # the transfer function falls monotonically through the interior
+    q = np.logspace(-3, 3, 200)
+    assert np.all(np.diff(_bbks_of_q(lcdm, q)) < 0)
+
+
 def test_time_grid_uniform_in_a():
     a, mid = time_grid(0.1, 1.0, 10)
     assert a[0] == 0.1 and a[-1] == 1.0 and len(a) == 11
