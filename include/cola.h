@@ -211,6 +211,15 @@ int cola_cross_power(cola_plan* plan, const float* delta_a, const float* delta_b
 int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t b_den, int32_t nmin, int32_t* group,
              int32_t* size, int32_t nthr, const int32_t* thresholds, int64_t* n_ge, cola_stream stream);
 
+/* Retry limit of the friends-of-friends union-find (this library's bounded loop; the paper has
+ * no counterpart): each union of two roots is attempted at most `tries` times (compare-and-swap
+ * rounds against concurrent unions) before cola_fof gives up on it and latches COLA_ETIMEOUT.
+ * Default 2^20.  tries = 0 makes every union give up at once, so that the failure path can be
+ * exercised without a fault: a run either reports COLA_ETIMEOUT through cola_status or its
+ * groups are exact.  0 <= tries <= 2^30 (COLA_EINVAL otherwise).  Host only; takes effect at the
+ * next cola_fof call on this plan. */
+int cola_set_fof_union_tries(cola_plan* plan, int32_t tries);
+
 /* Forward 3-D real-to-complex DFT (exp(-i k.x), unscaled) of a real mesh of side n, where
  * n is the plan's ng (which = 0) or np (which = 1).  in: device float32 [n^3]; out: device
  * complex64 [n][n][n/2+1] (interleaved re, im). */

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libcola_gb300.so")
 
 COLA_OK = 0
 COLA_NCOEF = 16
-ERRORS = {1: "COLA_EINVAL", 2: "COLA_ECUDA", 3: "COLA_EOVERFLOW", 4: "COLA_EUNSUPPORTED", 5: "COLA_ENOWORKSPACE"}
+ERRORS = {1: "COLA_EINVAL", 2: "COLA_ECUDA", 3: "COLA_EOVERFLOW", 4: "COLA_EUNSUPPORTED", 5: "COLA_ENOWORKSPACE",
+          6: "COLA_ETIMEOUT"}
 
 
 class ColaError(RuntimeError):
@@ -67,6 +68,7 @@ _SIGNATURES = {
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
     "cola_cross_power": [_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P],
     "cola_fof": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P],
+    "cola_set_fof_union_tries": [_P, ctypes.c_int32],
     "cola_status": [_P, _P],
     "cola_power_noalloc": [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P],
     "cola_step_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
@@ -212,6 +214,10 @@ def cola_fof(h, s, b_num, b_den, nmin, group, size, thresholds, n_ge, stream=Non
     _check(load_library().cola_fof(h, _ptr(s), int(b_num), int(b_den), int(nmin), _ptr(group), _ptr(size),
                                    int(thr.size), thr.ctypes.data_as(ctypes.c_void_p) if thr.size else None,
                                    _ptr(n_ge), _stream(stream)))
+
+
+def cola_set_fof_union_tries(h, tries):
+    _check(load_library().cola_set_fof_union_tries(h, int(tries)))
 
 
 def cola_fft_r2c(h, which, x, out, stream=None):

@@ -83,6 +83,8 @@ struct cola_plan {
   int64_t ng3 = 0;
   // the step gathers in bin order into the half-spectrum buffers (each holds np^3 floats)
   bool binned_gather = false;
+  // retry limit of the friends-of-friends union-find (cola_set_fof_union_tries)
+  int fof_union_tries = 1 << 20;
   std::vector<double> coef64;
   std::vector<float> coef32;
   std::vector<float2> tw_g, tw_p;

@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restric
     if (next < total && threadIdx.x < 32) issue(next, buf ^ 1);
     const bool ok = mbar_wait(&bars[buf], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
+      // leave no bulk copy in flight into shared memory the block releases: wait again (bounded)
+      // for the copy that timed out and for the next item's copy
       if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+      mbar_wait(&bars[buf], (it >> 1) & 1);
       if (next < total) mbar_wait(&bars[buf ^ 1], ((it + 1) >> 1) & 1);
       return;
     }

@@ -25,7 +25,6 @@ namespace cola {
 namespace {
 
 constexpr int kMaxThresholds = 32;
-constexpr int kUnionTries = 1 << 20;
 
 struct Thresholds {
   int n;
@@ -72,9 +71,9 @@ __device__ __forceinline__ int fof_find(const int* parent, int x) {
   return x;
 }
 
-// link the larger of the two roots under the smaller one; false if the retries ran out
-__device__ __forceinline__ bool fof_union(int* parent, int a, int b) {
-  for (int it = 0; it < kUnionTries; ++it) {
+// link the larger of the two roots under the smaller one; false if the `tries` attempts ran out
+__device__ __forceinline__ bool fof_union(int* parent, int a, int b, int tries) {
+  for (int it = 0; it < tries; ++it) {
     a = fof_find(parent, a);
     b = fof_find(parent, b);
     if (a == b) return true;
@@ -95,7 +94,8 @@ __device__ __forceinline__ int64_t min_image(int64_t d, int64_t period) {
 }
 
 __global__ void k_fof_link(Geometry g, const uint4* __restrict__ rec, const int* __restrict__ offsets, int csize,
-                           int nc, int64_t den2, int64_t lim, int* __restrict__ parent, int* __restrict__ err) {
+                           int nc, int64_t den2, int64_t lim, int tries, int* __restrict__ parent,
+                           int* __restrict__ err) {
   const int64_t n = g.np3;
   const int64_t period = (int64_t)g.ng << g.fbits;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -117,7 +117,7 @@ __global__ void k_fof_link(Geometry g, const uint4* __restrict__ rec, const int*
             const int64_t ey = min_image((int64_t)qj.y - fy, period);
             const int64_t ez = min_image((int64_t)qj.z - fz, period);
             const int64_t d2 = ex * ex + ey * ey + ez * ez;
-            if (den2 * d2 < lim) ok = fof_union(parent, (int)i, j) && ok;
+            if (den2 * d2 < lim) ok = fof_union(parent, (int)i, j, tries) && ok;
           }
         }
       }
@@ -217,8 +217,8 @@ extern "C" int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t 
   const int64_t lim = (int64_t)b_num * b_num * sfix * sfix;
   {
     LaunchScope ls_("fof_link", st);
-    k_fof_link<<<grid_of(n), 256, 0, st>>>(g, w.rec, offsets, csize, nc, (int64_t)b_den * b_den, lim, parent,
-                                           w.err);
+    k_fof_link<<<grid_of(n), 256, 0, st>>>(g, w.rec, offsets, csize, nc, (int64_t)b_den * b_den, lim,
+                                           plan->fof_union_tries, parent, w.err);
   }
   COLA_LAUNCH_CHECK();
   {
@@ -232,5 +232,12 @@ extern "C" int cola_fof(cola_plan* plan, const float* s, int32_t b_num, int32_t 
                                              reinterpret_cast<unsigned long long*>(n_ge));
   }
   COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+extern "C" int cola_set_fof_union_tries(cola_plan* plan, int32_t tries) {
+  if (!plan) return fail(COLA_EINVAL, "null plan");
+  if (tries < 0 || tries > (1 << 30)) return fail(COLA_EINVAL, "tries must be in [0, 2^30]");
+  plan->fof_union_tries = tries;
   return COLA_OK;
 }

@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 3)
     if (next < total && threadIdx.x < 32) c2r3_issue(c2r_stage + (b ^ 1) * RB * LD, src_of(next), RB, P, LD, &bars[b ^ 1]);
     const bool ok = mbar_wait(&bars[b], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
+      // leave no bulk copy in flight into shared memory the block releases: wait again (bounded)
+      // for the copy that timed out and for the next item's copy
       if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+      mbar_wait(&bars[b], (it >> 1) & 1);
       if (next < total) mbar_wait(&bars[b ^ 1], ((it + 1) >> 1) & 1);
       return;
     }

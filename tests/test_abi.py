@@ -34,6 +34,13 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(cdll, n), n
 
 
+def test_binding_names_every_error_code(lib):
+    text = open(os.path.join(ROOT, "include", "cola.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"#define\s+(COLA_E[A-Z]+)\s+(\d+)\s", text)}
+    assert codes and codes == lib.ERRORS
+    assert "COLA_ETIMEOUT" in str(lib.ColaError(6, "x"))
+
+
 def test_header_has_no_torch_types():
     text = open(os.path.join(ROOT, "include", "cola.h")).read()
     assert "torch" not in text.lower().replace("torch-", "")

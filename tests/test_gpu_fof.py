@@ -53,3 +53,35 @@ def test_fof_of_an_evolved_cola_box_and_other_linking_length(cola):
     nhalo = check(cola, plan, s32, n_p, ng, box)
     print("halos at z = 0 (32^3 particles, L = 25 Mpc/h):", nhalo)
     check(cola, plan, s32, n_p, ng, box, b=(1, 4), nmin=10)
+
+
+def test_union_retry_limit_reports_timeout_and_recovers(cola):
+    # The union-find is a bounded loop: when its retries run out, cola_fof latches COLA_ETIMEOUT
+    # (read by cola_status) instead of spinning.  With 0 tries every union gives up at once; with
+    # 1 try on a dense clump the run either reports the timeout or has exact groups; afterwards
+    # the default limit gives exact groups on the same plan (the context stays usable).
+    n_p, ng, box = 32, 64, 50.0
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box)
+    s32 = inputs.clustered_displacements(n_p, box, 3, nclump=2, frac=0.8, radius=0.3)
+    s_dev = torch.from_numpy(s32).cuda()
+    cola.cola_set_fof_union_tries(plan.handle, 0)
+    plan.fof(s_dev, nmin=25, b=(1, 5), thresholds=THRESHOLDS)
+    with pytest.raises(cola.ColaError) as e:
+        plan.status()
+    assert e.value.code == 6 and "union-find" in str(e.value)
+    cola.cola_set_fof_union_tries(plan.handle, 1)
+    group, size, n_ge = plan.fof(s_dev, nmin=25, b=(1, 5), thresholds=THRESHOLDS)
+    try:
+        plan.status()
+        exact = True
+    except cola.ColaError as err:
+        assert err.code == 6
+        exact = False
+    if exact:
+        f = omesh.fixed_point_coords(s32, n_p, ng, box, 16)
+        rg, _ = ofof.fof_groups(f, ng << 16, (ng // n_p) << 16, 25, 1, 5)
+        assert np.array_equal(group.cpu().numpy(), rg)
+    with pytest.raises(cola.ColaError):
+        cola.cola_set_fof_union_tries(plan.handle, -1)
+    cola.cola_set_fof_union_tries(plan.handle, 1 << 20)
+    assert check(cola, plan, s32, n_p, ng, box) >= 1
