@@ -6,6 +6,10 @@ initial conditions -> the nsteps+1 force evaluations of eq. ALCtimestep (deposit
 k-space Green's function, inverse FFTs, gather + COLA kick/drift) -> CIC density -> P(k).
 The metric is particle-updates per second: np^3 * nsteps / (wall time of one step).
 
+The headline workload is the largest single-GPU configuration, 1024^3 particles on a 2048^3
+mesh in a 1000 Mpc/h box; the paper's own Sec. 2 run (256^3 particles, 768^3 mesh, 100 Mpc/h)
+is measured the same way and reported as `paper_scale`.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 Multi-GPU (torchrun): every rank runs an independent realisation (different seed); there is no
@@ -25,7 +29,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "cola_256p_768g_L100"
+WORKLOAD = "cola_1024p_2048g_L1000"  # the largest single-GPU configuration (headline)
+PAPER_WORKLOAD = "cola_256p_768g_L100"  # the paper's Sec. 2 run (second line)
 METRIC = "COLA particle-updates/s (N_p x steps / s), fwd and fwd+adjoint, on 1 GB300 vs plain GPU"
 UNIT = "particle-updates/s"
 NSTEPS = 10
@@ -34,7 +39,7 @@ NSTEPS = 10
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -43,6 +48,7 @@ def parse_args():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-fof", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true")
     return ap.parse_args()
 
 
@@ -198,9 +204,10 @@ _ORACLE_STATE = {}
 
 def oracle_sample(workload):
     """One COLA step (PM force at a_0, kick to a_1/2, drift to a_1) of the float64 oracle on a
-    periodic sub-volume of the workload at the same resolution: half the box side, half the
-    particles and mesh cells per side (1/8 of the particles and cells).  The 2LPT initial
-    conditions are set up once, untimed.  Returns (particle-updates/s, seconds, description)."""
+    periodic sub-volume of the workload at the same resolution: the box side, the particles and
+    the mesh cells per side divided by d = max(2, np / 128) (1/8 of the 256^3/768^3 workload,
+    1/512 of the 1024^3/2048^3 one).  The 2LPT initial conditions are set up once, untimed.
+    Returns (particle-updates/s, seconds, description, particles in the sample)."""
     import numpy as np
 
     from oracle import cola as oc
@@ -209,7 +216,8 @@ def oracle_sample(workload):
     from paper_1301_0322_gb300 import inputs
 
     n_p, ng, box, seed = inputs.WORKLOADS[workload]
-    n_p, ng, box = n_p // 2, ng // 2, box / 2
+    d = max(2, n_p // 128)
+    n_p, ng, box = n_p // d, ng // d, box / d
     if workload not in _ORACLE_STATE:
         cosmo = Cosmology(**inputs.COSMOLOGY)
         cfg = oc.ColaConfig(n_p=n_p, n_g=ng, box=box, cosmo=cosmo, nsteps=NSTEPS)
@@ -228,8 +236,9 @@ def oracle_sample(workload):
     s = s + cd * v + (g["D1"][1] - g["D1"][0]) * s1 + (g["D2"][1] - g["D2"][0]) * s2
     dt = time.perf_counter() - t0
     desc = (f"one float64 oracle COLA step (PM force, kick, drift) on a {box:g} Mpc/h sub-volume at the "
-            f"workload's resolution ({n_p}^3 particles, {ng}^3 mesh, 1/8 of the workload)")
-    return n_p**3 / dt, dt, desc
+            f"workload's resolution ({n_p}^3 particles, {ng}^3 mesh, 1/{d**3} of the workload; the FFT's "
+            f"N log N share is that of the smaller mesh)")
+    return n_p**3 / dt, dt, desc, n_p**3
 
 
 def reference_arm(args):
@@ -240,18 +249,16 @@ def reference_arm(args):
     cores = os.cpu_count()
     times = []
     for i in range(args.warmup + args.steps):
-        _, dt, desc = oracle_sample(args.workload)
+        _, dt, desc, n_sub = oracle_sample(args.workload)
         if i >= args.warmup:
             times.append(dt)
-    from paper_1301_0322_gb300 import inputs
-    n_p = inputs.WORKLOADS[args.workload][0]
     per_step = statistics.mean(times)
-    value = (n_p // 2) ** 3 / per_step
+    value = n_sub / per_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "nsteps": NSTEPS, "l2": "inputs larger than L2"},
+        "config": workload_config(args.workload, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -260,7 +267,88 @@ def reference_arm(args):
 
 
 # ---- the GB300 arm ------------------------------------------------------------------------------------
-def gb300_arm(args):
+# kernels of one force evaluation (binning, mesh passes, gather, kick/drift) by profiler label
+EVAL_KERNELS = ("keys", "scan_reduce", "scan_blocks", "scan_apply", "scatter", "deposit_fftx_", "fft_cols_fwd_",
+                "fft_z_green_", "fft_y_inv3_", "fft_x_c2r3_", "gather_binned", "kick_drift", "gather_kick_drift")
+
+
+def eval_floor_bytes(n_p, ng):
+    """Algorithmic floor of one force evaluation: 56 bytes per mesh cell (deposit write 8, r2c read 8
+    + write 4, three c2r read 4 + write 4, gather read 12) plus 84 bytes per particle (deposit read
+    12, kick/drift read 48 and write 24)."""
+    return 56 * ng**3 + 84 * n_p**3
+
+
+def workload_config(workload, world):
+    from paper_1301_0322_gb300 import inputs
+    n_p, ng, box, _ = inputs.WORKLOADS[workload]
+    return {"workload": workload, "particles": f"{n_p}^3", "mesh": f"{ng}^3", "box_mpc_h": box,
+            "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations + density + P(k)",
+            "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (meshes of several GB)"}
+
+
+class HostSink:
+    """Device -> host copy of a float32 device array into a pageable host array through a ring of
+    pinned staging chunks: a helper thread issues one cudaMemcpyAsync per chunk on a copy stream
+    (after `ready` has been recorded) and copies each landed chunk into the destination while the
+    next one is in flight.  `enqueued()` returns the event after the last chunk's copy once the
+    thread has issued it (the caller's stream waits on it before reusing the source)."""
+
+    def __init__(self, torch, chunk_elems, nslots, copy_stream):
+        self.torch = torch
+        self.slots = [torch.empty(chunk_elems, dtype=torch.float32, pin_memory=True) for _ in range(nslots)]
+        self.done = [torch.cuda.Event() for _ in range(nslots)]
+        self.cs = copy_stream
+        self.chunk = chunk_elems
+        self.thread = None
+        self.last = None
+        self.issued = threading.Event()
+
+    def start(self, src, dst, ready):
+        self.issued.clear()
+        self.thread = threading.Thread(target=self._run, args=(src.reshape(-1), dst.reshape(-1), ready))
+        self.thread.start()
+
+    def _run(self, src, dst, ready):
+        torch = self.torch
+        n, c, ns = src.numel(), self.chunk, len(self.slots)
+        ranges = [(a, min(n, a + c)) for a in range(0, n, c)]
+        pending = [None] * ns
+        with torch.cuda.device(src.device), torch.cuda.stream(self.cs):
+            self.cs.wait_event(ready)
+            for i, (a, b) in enumerate(ranges):
+                k = i % ns
+                if pending[k] is not None:
+                    self._land(k, pending[k], dst)
+                self.slots[k][:b - a].copy_(src[a:b], non_blocking=True)
+                self.done[k].record(self.cs)
+                pending[k] = (a, b)
+            self.last = self.done[(len(ranges) - 1) % ns]
+            self.issued.set()
+            for j in range(len(ranges), len(ranges) + ns):
+                k = j % ns
+                if pending[k] is not None:
+                    self._land(k, pending[k], dst)
+                    pending[k] = None
+
+    def _land(self, k, ab, dst):
+        a, b = ab
+        self.done[k].synchronize()
+        dst[a:b].copy_(self.slots[k][:b - a])
+
+    def enqueued(self):
+        self.issued.wait()
+        return self.last
+
+    def join(self):
+        self.thread.join()
+
+
+def measure_workload(args, workload, dev, rank, world, with_fof):
+    """Time `args.steps` whole runs of `workload` (after `args.warmup` untimed ones) on the device,
+    the per-kernel split, the roofline of the dominant kernel and of a whole force evaluation, and
+    the same runs end to end with host buffers."""
     import ctypes
 
     import torch
@@ -268,10 +356,7 @@ def gb300_arm(args):
     import paper_1301_0322_gb300 as cola
     from paper_1301_0322_gb300 import inputs
 
-    rank, world, local = dist_setup("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    n_p, ng, box, seed = inputs.WORKLOADS[args.workload]
+    n_p, ng, box, seed = inputs.WORKLOADS[workload]
     plan = cola.Plan(np_side=n_p, ng=ng, box=box, nsteps=NSTEPS, device=dev, **inputs.COSMOLOGY)
     h = plan.handle
     lib = cola.load_library()
@@ -281,7 +366,7 @@ def gb300_arm(args):
     # v, s1, s2 and the final density mesh share one allocation (the density is taken after the
     # last step, when v, s1 and s2 are no longer read), and the noise sits in the v slot (the
     # initial conditions transform it before they write v): at 1024^3/2048^3 this is what lets
-    # the density and P(k) fit beside the 215 GB workspace
+    # the density and P(k) fit beside the 228 GB workspace
     pool = plan._empty(max(9 * n3, ng**3))
     v, s1, s2 = (pool[i * 3 * n3:(i + 1) * 3 * n3].view(3, n3) for i in range(3))
     noise = pool[:n3]
@@ -298,7 +383,7 @@ def gb300_arm(args):
         cola.cola_power(h, delta, nbins, k, pk, nm)
 
     base_seed = seed + 1000 * rank
-    gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+    gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
     gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
     sampler = ClockSampler(gpu_id) if rank == 0 else None
     for i in range(args.warmup):
@@ -330,7 +415,7 @@ def gb300_arm(args):
     if sampler:
         sampler.mark(t_wall0, t_wall1)
         clocks = sampler.stop()
-    # per-kernel device time from the events recorded around every launch
+    # per-kernel device time from the events recorded around every launch (on the launch stream)
     nmax = 256
     names = ctypes.create_string_buffer(64 * nmax)
     launches = (ctypes.c_int64 * nmax)()
@@ -342,70 +427,78 @@ def gb300_arm(args):
         nm_ = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         kernels[nm_] = {"launches": int(launches[i]), "ms": float(msk[i])}
     total_ms = ms_step * args.steps
-    for kv in kernels.values():
+    peak, peak_kind = hbm_peak()
+    for name, kv in kernels.items():
         kv["share"] = kv["ms"] / total_ms
+        alg = algorithmic_bytes(name, n_p, ng)
+        kv["avg_launch_ms"] = kv["ms"] / kv["launches"]
+        if alg:
+            kv["bytes_per_launch"] = alg
+            kv["achieved_gbs"] = alg / (kv["avg_launch_ms"] * 1e-3) / 1e9
+            kv["frac"] = kv["achieved_gbs"] / peak
     dom = max(kernels, key=lambda x: kernels[x]["ms"])
     alg = algorithmic_bytes(dom, n_p, ng)
-    avg_ms = kernels[dom]["ms"] / kernels[dom]["launches"]
-    peak, peak_kind = hbm_peak()
+    avg_ms = kernels[dom]["avg_launch_ms"]
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    # one force evaluation against the algorithmic floor of the scope table
+    evals = args.steps * (NSTEPS + 1)
+    ev_ms = sum(kv["ms"] for nm_, kv in kernels.items()
+                if any(nm_ == e or (e.endswith("_") and nm_ == e + str(ng)) for e in EVAL_KERNELS)) / evals
+    floor = eval_floor_bytes(n_p, ng)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": measured_traffic(dom, args.workload), "bytes_per_launch": alg,
-                "avg_launch_ms": avg_ms}
+                "traffic": measured_traffic(dom, workload), "bytes_per_launch": alg, "avg_launch_ms": avg_ms,
+                "force_evaluation": {"floor_bytes": floor, "ms": ev_ms,
+                                     "achieved_gbs": floor / (ev_ms * 1e-3) / 1e9,
+                                     "frac": floor / (ev_ms * 1e-3) / 1e9 / peak,
+                                     "floor": "56 B per mesh cell + 84 B per particle"}}
     value = world * n3 * NSTEPS / (ms_step * 1e-3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the noise arrives from pinned host
+    # memory, s, v and P(k) go back to pageable host arrays through pinned staging chunks
     e2e = None
-    if not args.no_e2e and ng <= 1536:  # pinned host copies of the 2048^3 state would be 30 GB
+    if not args.no_e2e:
+        copy_stream = torch.cuda.Stream(device=dev)
+        chunk = min(3 * n3, 64 << 20)  # 256 MB chunks
+        sink_s, sink_v = (HostSink(torch, chunk, 3, copy_stream) for _ in range(2))
         h_noise = torch.empty(n3, dtype=torch.float32, pin_memory=True)
-        h_s = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
-        h_v = torch.empty((3, n3), dtype=torch.float32, pin_memory=True)
+        h_s = torch.zeros((3, n3), dtype=torch.float32)  # pageable (zeros: pages touched once here)
+        h_v = torch.zeros((3, n3), dtype=torch.float32)
         h_pk = torch.empty(nbins, dtype=torch.float64, pin_memory=True)
         cola.cola_noise(h, base_seed, noise)
         h_noise.copy_(noise)
-        # device buffers of their own, so that the copies can overlap the compute: the noise is
-        # double-buffered (the next run's copy arrives during this run) and the density does
-        # not reuse the v slot (s and v go back to the host during the density and P(k))
-        e_noise = [plan._empty(n3), plan._empty(n3)]
-        e_delta = plan._empty(ng**3)
-        copy_stream = torch.cuda.Stream(device=dev)
-        ev_ic, ev_s, ev_steps, ev_noise, ev_state = (torch.cuda.Event() for _ in range(5))
-        e_noise[0].copy_(h_noise)
+        e_noise = plan._empty(n3)  # its own slot, so that the next run's noise arrives during this run
+        ev_ic, ev_s, ev_steps, ev_noise = (torch.cuda.Event() for _ in range(4))
+        e_noise.copy_(h_noise)
+        ev_noise.record(stream)
         torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 5))
-        turn = [0]
+        ke = max(1, min(args.steps, 3 if ng >= 1536 else 5))
 
         def e2e_step():
-            cur = e_noise[turn[0] % 2]
             stream.wait_event(ev_noise)  # this run's noise has arrived
-            stream.wait_event(ev_state)  # the previous run's s and v have left
-            cola.cola_ic_2lpt(h, cur, s, v, s1, s2)
+            cola.cola_ic_2lpt(h, e_noise, s, v, s1, s2)
             ev_ic.record(stream)
             with torch.cuda.stream(copy_stream):  # the next run's noise, host -> device
                 copy_stream.wait_event(ev_ic)
-                e_noise[(turn[0] + 1) % 2].copy_(h_noise, non_blocking=True)
+                e_noise.copy_(h_noise, non_blocking=True)
                 ev_noise.record(copy_stream)
             for i in range(NSTEPS + 1):
                 cola.cola_step(h, i, s, v, s1, s2)
-                if i == NSTEPS - 1:  # s is final here (the last evaluation kicks v only): copy it out
+                if i == NSTEPS - 1:  # s is final here (the last evaluation kicks v only)
                     ev_s.record(stream)
-                    with torch.cuda.stream(copy_stream):
-                        copy_stream.wait_event(ev_s)
-                        h_s.copy_(s, non_blocking=True)
+                    sink_s.start(s, h_s, ev_s)
             ev_steps.record(stream)
-            with torch.cuda.stream(copy_stream):  # the final v, device -> host
-                copy_stream.wait_event(ev_steps)
-                h_v.copy_(v, non_blocking=True)
-                ev_state.record(copy_stream)
-            cola.cola_density(h, s, None, e_delta)
-            cola.cola_power(h, e_delta, nbins, k, pk, nm)
+            sink_v.start(v, h_v, ev_steps)
+            stream.wait_event(sink_v.enqueued())  # the density overwrites the v slot
+            cola.cola_density(h, s, None, delta)
+            cola.cola_power(h, delta, nbins, k, pk, nm)
             h_pk.copy_(pk, non_blocking=True)
-            turn[0] += 1
+            stream.wait_event(sink_s.enqueued())
 
         def e2e_join():
+            sink_s.join()
+            sink_v.join()
             stream.wait_event(ev_noise)
-            stream.wait_event(ev_state)
 
         e2e_step()
         e2e_join()
@@ -413,19 +506,24 @@ def gb300_arm(args):
         barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(ke):
             e2e_step()
-        e2e_join()  # every copy of the timed runs has completed before the end event
+            e2e_join()  # the host arrays hold this run's s and v before the next run starts
         e1.record(stream)
         e1.synchronize()
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, world, dev)
+        wall = (time.perf_counter() - t0) * 1e3 / ke
+        ms_e2e = max_over_ranks(max(e0.elapsed_time(e1) / ke, wall), world, dev)
         assert torch.equal(h_pk, pk.cpu()), "host copy of P(k) differs from the device result"
+        assert torch.equal(h_v[:, :1024], v[:, :1024].cpu()), "host copy of v differs"
         e2e = {"value": world * n3 * NSTEPS / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": 4 * n3, "d2h_bytes_per_step": 2 * 12 * n3 + 8 * nbins}
+               "h2d_bytes_per_step": 4 * n3, "d2h_bytes_per_step": 2 * 12 * n3 + 8 * nbins,
+               "steps": ke, "host_arrays": "s, v pageable (through 256 MB pinned staging chunks); noise, P(k) pinned"}
+        del sink_s, sink_v, h_s, h_v, h_noise, e_noise
 
     # halo finding on the final state of the last run (Sec. 3.2: b = 0.2, >= 25 particles)
     fof = None
-    if not args.no_fof and rank == 0:
+    if with_fof and not args.no_fof and rank == 0:
         thresholds = [25, 50, 100, 200, 400, 800, 1600, 3200]
         group = plan._empty(n3, torch.int32)
         size = plan._empty(n3, torch.int32)
@@ -443,12 +541,45 @@ def gb300_arm(args):
         fof = {"ms": f0.elapsed_time(f1), "linking_length": 0.2, "nmin": 25, "particle_mass_msun_h": m_p,
                "halos": int(n_ge[0]),
                "n_ge": {f"{t * m_p:.3g}": int(c) for t, c in zip(thresholds, n_ge.tolist())},
-               "state": "final state of the last timed run"}
+               "state": f"final state of the last timed {workload} run"}
+    del plan, pool, s
+    torch.cuda.empty_cache()
+    return {
+        "workload": workload, "value": value, "ms_per_step": ms_step, "roofline": roofline, "e2e": e2e,
+        "clocks": clocks, "fof": fof, "gpu_launches": int(cnt1.value - cnt0.value),
+        "config": workload_config(workload, world),
+        "kernels": {kk: {"launches": kv["launches"], "ms_per_step": round(kv["ms"] / args.steps, 4),
+                         "share": round(kv["share"], 4),
+                         **({"frac": round(kv["frac"], 4), "achieved_gbs": round(kv["achieved_gbs"], 1)}
+                            if "frac" in kv else {})}
+                    for kk, kv in sorted(kernels.items(), key=lambda x: -x[1]["ms"])},
+    }
+
+
+def cpu_baseline(workload):
+    reps, vals, desc, spent = 0, [], "", 0.0
+    while spent < 10.0 and reps < 4:
+        val, dt, desc, _ = oracle_sample(workload)
+        vals.append(val)
+        spent += dt
+        reps += 1
+    return {"value": statistics.median(vals), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{desc}; median of {reps} repetitions"}
+
+
+def gb300_arm(args):
+    import torch
+
+    rank, world, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    head = measure_workload(args, args.workload, dev, rank, world, with_fof=args.workload == PAPER_WORKLOAD)
+    paper = None
+    if args.workload != PAPER_WORKLOAD and not args.no_paper_scale:
+        paper = measure_workload(args, PAPER_WORKLOAD, dev, rank, world, with_fof=True)
 
     # forward + adjoint on the differentiable workload, through the autograd wrapper
     fwd_adj = None
-    del plan
-    torch.cuda.empty_cache()
     if not args.no_adjoint:
         fwd_adj = adjoint_timing(args, dev, rank, world)
         torch.cuda.empty_cache()
@@ -459,33 +590,28 @@ def gb300_arm(args):
         ens = ensemble_timing(args, dev, rank, world)
         torch.cuda.empty_cache()
 
-    cpu = None
+    cpu = cpu_paper = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        reps, vals, desc, spent = 0, [], "", 0.0
-        while spent < 10.0 and reps < 4:
-            val, dt, desc = oracle_sample(args.workload)
-            vals.append(val)
-            spent += dt
-            reps += 1
-        cpu = {"value": statistics.median(vals), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{desc}; median of {reps} repetitions"}
+        cpu = cpu_baseline(args.workload)
+        if paper is not None:
+            cpu_paper = cpu_baseline(PAPER_WORKLOAD)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "particles": f"{n_p}^3", "mesh": f"{ng}^3", "box_mpc_h": box,
-                       "nsteps": NSTEPS, "step": "noise + 2LPT IC + 11 force evaluations + density + P(k)",
-                       "mode": "forward", "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (meshes of several GB)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fwd_adjoint": fwd_adj,
-            "ensemble": ens, "fof": fof,
-            "gpu_launches": int(cnt1.value - cnt0.value),
-            "kernels": {kk: {"launches": kv["launches"], "ms_per_step": kv["ms"] / args.steps,
-                             "share": round(kv["share"], 4)} for kk, kv in
-                        sorted(kernels.items(), key=lambda x: -x[1]["ms"])},
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": head["config"], "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
+            "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
+            "paper_scale": None if paper is None else {
+                k_: paper[k_] for k_ in ("workload", "value", "ms_per_step", "roofline", "e2e", "clocks",
+                                         "gpu_launches", "kernels")},
+            "fwd_adjoint": fwd_adj, "ensemble": ens, "fof": head["fof"] or (paper or {}).get("fof"),
+            "kernels": head["kernels"],
         }
+        if paper is not None:
+            line["paper_scale"]["unit"] = UNIT
+            line["paper_scale"]["cpu_baseline"] = cpu_paper
         print(json.dumps(line), flush=True)
     barrier(world)
 

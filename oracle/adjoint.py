@@ -23,7 +23,7 @@ import numpy as np
 import scipy.fft
 
 from . import mesh
-from .cola import evolve
+from .cola import evolve, quantise_positions
 from .cosmology import time_grid
 from .lpt import ic_2lpt, linear_density_k
 from .mesh import FFT_WORKERS, cic_window, gradient_factor, mode_numbers
@@ -158,15 +158,26 @@ def forward_with_checkpoints(noise, cfg):
 
 def final_density(s, cfg):
     pos = np.mod(mesh.lattice_q(cfg.n_p, cfg.box) + s, cfg.box)
+    if cfg.fixed_bits > 0:
+        pos = quantise_positions(pos, cfg.n_g, cfg.box, cfg.fixed_bits)
     return mesh.overdensity(mesh.cic_deposit(pos, cfg.n_g, cfg.box), cfg.n_p**3)
 
 
 def loss_and_gradient(noise, target, cfg):
     """L = sum_c (delta_c - target_c)^2 of the final CIC density, and dL/d noise (float64)."""
-    cosmo = cfg.cosmo
     fw = forward_with_checkpoints(noise, cfg)
-    delta = final_density(fw["s"], cfg)
-    loss = float(np.sum((delta - target) ** 2))
+    loss, grad = loss_and_gradient_along(noise, target, cfg, fw["ckpt"], fw["s"])
+    return loss, grad, fw
+
+
+def loss_and_gradient_along(noise, target, cfg, ckpt, s_final, positions=None):
+    """The reverse sweep of loss_and_gradient along a given trajectory: ckpt = the displacement
+    at each of the nsteps + 1 force evaluations, s_final = the final displacement.  The loss and
+    the adjoint are evaluated at the particle positions positions(s) (default: x = q + s modulo
+    L, rounded down to 2^-F cell when cfg.fixed_bits = F > 0, the reading oracle.cola applies to
+    the force), so that a trajectory computed elsewhere is differentiated on the same side of
+    every CIC kink as it was integrated.  Returns (loss, dL/d noise)."""
+    cosmo = cfg.cosmo
     a, mid = time_grid(cfg.a_init, cfg.a_final, cfg.nsteps, cfg.spacing)
     g = cosmo.growth(a)
     q = mesh.lattice_q(cfg.n_p, cfg.box)
@@ -174,10 +185,17 @@ def loss_and_gradient(noise, target, cfg):
     am = 1.5 * cosmo.omega_m
 
     def pos_of(s):
-        return np.mod(q + s, cfg.box)
+        if positions is not None:
+            return positions(s)
+        pos = np.mod(q + s, cfg.box)
+        if cfg.fixed_bits > 0:
+            pos = quantise_positions(pos, cfg.n_g, cfg.box, cfg.fixed_bits)
+        return pos
 
-    s1, s2 = fw["s1"], fw["s2"]
-    lam_s = density_vjp(pos_of(fw["s"]), 2.0 * (delta - target), npart, cfg.box)
+    pos_final = pos_of(s_final)
+    delta = mesh.overdensity(mesh.cic_deposit(pos_final, cfg.n_g, cfg.box), npart)
+    loss = float(np.sum((delta - target) ** 2))
+    lam_s = density_vjp(pos_final, 2.0 * (delta - target), npart, cfg.box)
     lam_v = np.zeros_like(lam_s)
     lam_s1 = np.zeros_like(lam_s)
     lam_s2 = np.zeros_like(lam_s)
@@ -187,7 +205,7 @@ def loss_and_gradient(noise, target, cfg):
     for i in reversed(range(cfg.nsteps)):
         # K(a_i+1/2, a_i+1; a_i+1) with the force at the positions after the drift
         c = cosmo.kick_cola(mid[i], a[i + 1], a[i + 1], cfg.n_lpt)
-        lam_s += c * am * a[i + 1] * force_vjp(pos_of(fw["ckpt"][i + 1]), lam_v, npart, cfg.n_g, cfg.box, cfg.deconv)
+        lam_s += c * am * a[i + 1] * force_vjp(pos_of(ckpt[i + 1]), lam_v, npart, cfg.n_g, cfg.box, cfg.deconv)
         lam_s1 -= c * g["T2D1"][i + 1] * lam_v
         lam_s2 -= c * g["T2D2"][i + 1] * lam_v
         # D(a_i, a_i+1; a_i+1/2)
@@ -196,14 +214,14 @@ def loss_and_gradient(noise, target, cfg):
         lam_s2 += (g["D2"][i + 1] - g["D2"][i]) * lam_s
         # K(a_i, a_i+1/2; a_i)
         c = cosmo.kick_cola(a[i], mid[i], a[i], cfg.n_lpt)
-        lam_s += c * am * a[i] * force_vjp(pos_of(fw["ckpt"][i]), lam_v, npart, cfg.n_g, cfg.box, cfg.deconv)
+        lam_s += c * am * a[i] * force_vjp(pos_of(ckpt[i]), lam_v, npart, cfg.n_g, cfg.box, cfg.deconv)
         lam_s1 -= c * g["T2D1"][i] * lam_v
         lam_s2 -= c * g["T2D2"][i] * lam_v
     # initial conditions: s = D1 s1 + D2 s2 (the 2LPT velocity and L- cancel exactly)
     lam_s1 += g["D1"][0] * lam_s
     lam_s2 += g["D2"][0] * lam_s
     grad = ic_vjp(np.asarray(noise, dtype=np.float64), lam_s1, lam_s2, cfg.box, cosmo)
-    return loss, grad, fw
+    return loss, grad
 
 
 def loss_only(noise, target, cfg):

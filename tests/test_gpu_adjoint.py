@@ -3,14 +3,19 @@ of the gradient with respect to the white noise against central finite differenc
 
 Tolerances: the GPU differentiates the CIC weights at positions quantised to 2^-16 cell and
 runs float32 FFTs; each adjoint piece agrees with the oracle's to <= 3e-4 of its largest
-entry (as the forward force does).  The loss of a full run is only piecewise smooth: every
-CIC cell face a particle crosses is a kink, and the gradient exists almost everywhere.  Two
-runs whose particles differ by ~1e-5 cell (the GPU's quantisation and float32 rounding,
-amplified by the dynamics) therefore differentiate on different sides of a few kinks: measured
-on 32^3/64^3, the GPU gradient is within 3.9e-3 (L2) of the float64 oracle gradient at
-a = 0.5 and within 1.8e-2 at a = 1, where even float64 central differences of the oracle
-scatter by 0.3-5% around its exact adjoint (4e-5 - 1.4e-3 at a = 0.5).  Central differences
-of the GPU forward itself also carry its 2^-16-cell quantisation steps.
+entry (as the forward force does).  The whole gradient is held to the 1e-3 target in two ways:
+  * against the float64 oracle adjoint run along the GPU's own trajectory (its checkpoints and
+    fixed-point positions), so that both sides differentiate the same piecewise-smooth map;
+  * against float64 central differences of the oracle forward in the smooth regime (a_final =
+    0.3, 3 steps), where central differences resolve 1e-3 (3e-5 for the oracle's own adjoint).
+The loss of a full run to a = 1 is only piecewise smooth: every CIC cell face a particle crosses
+is a kink.  Two runs whose particles differ by ~1e-5 cell (the GPU's quantisation and float32
+rounding, amplified by the dynamics) differentiate on different sides of a few kinks: measured
+on 32^3/64^3, the GPU gradient is within 3.9e-3 (L2) of the float64 oracle gradient of the
+unquantised trajectory at a = 0.5 and within 1.8e-2 at a = 1, where even float64 central
+differences of the oracle scatter by 0.3-5% around its exact adjoint.  Central differences of
+the GPU forward also carry its 2^-16-cell quantisation steps; the 128^3/256^3 check against them
+is held to that measured floor.
 """
 import numpy as np
 import pytest
@@ -119,6 +124,85 @@ def test_full_gradient_matches_oracle(cola, a_final, min_cos, max_rel):
     assert cos > min_cos and rel < max_rel
 
 
+def gpu_trajectory(plan, noise):
+    """The GPU forward run of ColaDensity, keeping the displacement of every force evaluation
+    (the same launches, hence bit for bit the trajectory the backward pass differentiates)."""
+    s, v, s1, s2 = plan.ic_2lpt(noise)
+    ckpt = []
+    for i in range(plan.nsteps + 1):
+        ckpt.append(host(s))
+        plan.step(i, s, v, s1, s2)
+    plan.status()
+    return ckpt, host(s)
+
+
+@pytest.mark.parametrize("n_p,ng,box,a_final,nsteps", [(32, 64, 100.0, 1.0, 10), (32, 64, 100.0, 0.5, 10),
+                                                        (64, 128, 200.0, 1.0, 10)])
+def test_gradient_matches_oracle_along_the_gpu_trajectory(cola, n_p, ng, box, a_final, nsteps):
+    # Both sides differentiate the same trajectory: the float64 oracle adjoint sweep runs along
+    # the GPU's own checkpoints at the GPU's fixed-point positions (2^-16 cell), so every CIC
+    # kink is taken on the same side and what is left is the float32 rounding of the GPU
+    # adjoint.  Target: relative L2 error <= 1e-3 of the gradient with respect to the noise.
+    cosmo = Cosmology(**inputs.COSMOLOGY)
+    cfg = ColaConfig(n_p=n_p, n_g=ng, box=box, cosmo=cosmo, a_final=a_final, nsteps=nsteps, fixed_bits=16)
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, adjoint=True, a_final=a_final, nsteps=nsteps)
+    with torch.no_grad():
+        target = cola.cola_density_from_noise(dev(inputs.gaussian_noise(n_p, 7)), plan).double()
+    w = inputs.gaussian_noise(n_p, 1)
+    x = dev(w).requires_grad_(True)
+    loss = ((cola.cola_density_from_noise(x, plan).double() - target) ** 2).sum()
+    loss.backward()
+    g = host(x.grad).reshape(-1)
+    ckpt, s_final = gpu_trajectory(plan, dev(w))
+    unit = box / ng / 2.0**16
+
+    def positions(s):
+        return omesh.fixed_point_coords(s.astype(np.float32), n_p, ng, box, 16) * unit
+
+    lref, gref = oa.loss_and_gradient_along(w.reshape(n_p, n_p, n_p).astype(np.float64),
+                                            host(target).reshape(ng, ng, ng), cfg, ckpt, s_final, positions)
+    gref = gref.reshape(-1)
+    rel = float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+    cos = float(g @ gref / np.linalg.norm(g) / np.linalg.norm(gref))
+    print(f"{n_p}^3/{ng}^3, a = {a_final}: gradient vs oracle along the GPU trajectory: relative L2 {rel:.2e}, "
+          f"cosine {cos:.9f}, loss {float(loss):.6e} vs {lref:.6e}")
+    assert abs(float(loss) / lref - 1.0) <= 1e-5
+    assert rel <= 1e-3
+
+
+def test_gradient_matches_float64_central_differences_smooth_regime(cola):
+    # Where the map is smooth enough for central differences to resolve 1e-3 -- early times
+    # and few steps (a_final = 0.3, 3 steps; the float64 oracle's own central differences with
+    # eps = 1e-6 agree with its exact adjoint to 3e-5 of the rms projection there) -- the GPU
+    # gradient projected on 16 random low-k Fourier modes of the noise agrees with float64
+    # central differences of the oracle forward map to 1e-3 of the rms projection.  (Central
+    # differences of the GPU forward itself cannot resolve 1e-3: its positions move in 2^-16
+    # cell steps, and any eps large enough to span many steps lets a fraction of the particles
+    # cross CIC cell faces, whose kinks bias the difference quotient.)
+    n_p, ng, box, a_final, nsteps = 32, 64, 100.0, 0.3, 3
+    cosmo = Cosmology(**inputs.COSMOLOGY)
+    cfg = ColaConfig(n_p=n_p, n_g=ng, box=box, cosmo=cosmo, a_final=a_final, nsteps=nsteps)
+    w = inputs.gaussian_noise(n_p, 1)
+    w64 = w.reshape(n_p, n_p, n_p).astype(np.float64)
+    target = oa.final_density(oa.forward_with_checkpoints(
+        inputs.gaussian_noise(n_p, 7).reshape(n_p, n_p, n_p).astype(np.float64), cfg)["s"], cfg)
+    plan = cola.Plan(np_side=n_p, ng=ng, box=box, adjoint=True, a_final=a_final, nsteps=nsteps)
+    x = dev(w).requires_grad_(True)
+    loss = ((cola.cola_density_from_noise(x, plan).double() - dev(target.reshape(-1))) ** 2).sum()
+    loss.backward()
+    g = host(x.grad)
+    eps, fd, an = 1e-6, [], []
+    for m in range(16):
+        e = fourier_mode(n_p, 100 + m).astype(np.float64).reshape(n_p, n_p, n_p)
+        fd.append((oa.loss_only(w64 + eps * e, target, cfg) - oa.loss_only(w64 - eps * e, target, cfg)) / (2 * eps))
+        an.append(float(g @ e.reshape(-1)))
+    fd, an = np.array(fd), np.array(an)
+    err = np.abs(fd - an) / np.sqrt(np.mean(fd**2))
+    print(f"a = {a_final}, {nsteps} steps: |fd - adj| / rms(fd) on 16 modes: max {err.max():.2e}, "
+          f"median {np.median(err):.2e}")
+    assert err.max() <= 1e-3
+
+
 def fourier_mode(n, seed):
     rng = np.random.default_rng(seed)
     kvec = rng.integers(-n // 4, n // 4 + 1, size=3)
@@ -159,6 +243,8 @@ def test_gradient_matches_central_differences_128p_256g(cola):
     corr = float(np.corrcoef(fd, an)[0, 1])
     print(f"central differences on 64 modes: correlation {corr:.5f}, median |fd - adj| / rms(adj) "
           f"{np.median(err):.2e}, max {err.max():.2e}")
-    # measured on GB300: correlation 0.986, median 4e-2 (the kink and quantisation floor above)
+    # the kink and quantisation floor of central differences at a = 1 (module docstring):
+    # measured on GB300, correlation 0.986 and median 4e-2; the float64 oracle's own central
+    # differences scatter by 0.3-5% around its exact adjoint in the same regime at 32^3/64^3
     assert corr > 0.97
     assert np.median(err) < 0.1
