@@ -9,7 +9,8 @@ from .cola import (COLA_NCOEF, ColaDensity, ColaError, Ensemble, Plan, cola_coef
                    cola_ensemble_workspace_bytes, cola_ensemble_set_workspace, cola_ensemble_offsets,
                    cola_ensemble_noise, cola_ensemble_ic_2lpt, cola_ensemble_step, cola_ensemble_density,
                    cola_ensemble_power, cola_ensemble_tune, cola_ensemble_get_tuning, cola_ensemble_set_tuning,
-                   cola_ensemble_use_graphs, cola_ensemble_status, cola_cross_power, cola_fof)
+                   cola_ensemble_use_graphs, cola_ensemble_status, cola_cross_power, cola_fof,
+                   cola_set_fof_union_tries)
 
 __all__ = ["Plan", "Ensemble", "ColaError", "ColaDensity", "COLA_NCOEF", "load_library", "cola_config_default",
            "cola_plan_create", "cola_plan_destroy", "cola_workspace_bytes", "cola_set_workspace", "cola_coeffs",
@@ -19,4 +20,5 @@ __all__ = ["Plan", "Ensemble", "ColaError", "ColaDensity", "COLA_NCOEF", "load_l
            "cola_ensemble_workspace_bytes", "cola_ensemble_set_workspace", "cola_ensemble_offsets",
            "cola_ensemble_noise", "cola_ensemble_ic_2lpt", "cola_ensemble_step", "cola_ensemble_density",
            "cola_ensemble_power", "cola_ensemble_tune", "cola_ensemble_get_tuning", "cola_ensemble_set_tuning",
-           "cola_ensemble_use_graphs", "cola_ensemble_status", "cola_cross_power", "cola_fof"]
+           "cola_ensemble_use_graphs", "cola_ensemble_status", "cola_cross_power", "cola_fof",
+           "cola_set_fof_union_tries"]

@@ -187,12 +187,14 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   p->geo.ratio = (c.ng % c.np == 0) ? (int)(c.ng / c.np) : 0;
   p->geo.scale32 = (float)((double)c.ng / c.box);
   p->ng3 = c.ng * c.ng * c.ng;
-  // deposit tiles of 4 x 2 mesh rows (y, z), each spanning the whole x extent
-  p->tiles.ty = 4;
+  // deposit tiles of 4 x 2 mesh rows (y, z), each spanning the whole x extent (2 x 2 at ng = 2048,
+  // where a 4 x 2 tile of int64 cells fills the shared memory of an SM: two blocks per SM)
+  p->tiles.ty = c.ng == 2048 ? 2 : 4;
   p->tiles.tz = 2;
-  p->tiles.nty = (int)c.ng / 4;
+  p->tiles.nty = (int)c.ng / p->tiles.ty;
   p->tiles.ntz = (int)c.ng / 2;
   p->tiles.nbins = p->tiles.nty * p->tiles.ntz * 4;
+  p->tiles.lband = tile_band_log2(p->tiles.nty);
   p->Pg = padded_half((int)c.ng);
   p->Pp = padded_half((int)c.np);
   p->binned_gather = (double)sizeof(float2) * c.ng * c.ng * p->Pg >= (double)sizeof(float) * p->geo.np3;

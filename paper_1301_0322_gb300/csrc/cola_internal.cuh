@@ -42,7 +42,28 @@ struct Tiles {
   int ty, tz;     // rows per tile along y and z (the tile spans the whole x row)
   int nty, ntz;   // tiles per axis
   int nbins;      // nty * ntz * 4 (4 boundary regions per tile)
+  int lband;      // log2 of the tiles per band along y (bins run band by band, see tile_bin)
 };
+
+// Tiles are numbered band by band: a band is 2^lband consecutive tiles along y, and within a band
+// the tiles run along y, then z.  Consecutive bins then cover the whole z range of a narrow band
+// of y rows, so the rows that neighbouring tiles share along z (and y) are still in L2 when the
+// next tile reads them.
+__host__ __device__ __forceinline__ int tile_bin(const Tiles& tl, int ty, int tz) {
+  return (((ty >> tl.lband) * tl.ntz + tz) << tl.lband) + (ty & ((1 << tl.lband) - 1));
+}
+__host__ __device__ __forceinline__ void tile_of_bin(const Tiles& tl, int bin, int& ty, int& tz) {
+  const int per_band = tl.ntz << tl.lband;
+  const int band = bin / per_band, rem = bin - band * per_band;
+  tz = rem >> tl.lband;
+  ty = (band << tl.lband) + (rem & ((1 << tl.lband) - 1));
+}
+// the largest power of two <= 32 that divides nty
+inline int tile_band_log2(int nty) {
+  int l = 0;
+  while (l < 5 && nty % (2 << l) == 0) ++l;
+  return l;
+}
 
 struct Workspace {
   float2* tw_g = nullptr;   // exp(-2 pi i m / ng), m < ng

@@ -463,6 +463,7 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     d.tl.nty = n / sh.ty;
     d.tl.ntz = n / sh.tz;
     d.tl.nbins = d.tl.nty * d.tl.ntz * 4;
+    d.tl.lband = tile_band_log2(d.tl.nty);
     d.P = p->Pg;
     d.deconv = p->cfg.deconv;
     d.bin_base = bins;

@@ -203,6 +203,16 @@ template <int N, int E, int TWS, bool INV>
 struct Stockham {
   static constexpr int T = N / E;
 
+  // Butterfly j = t + T q of a stage (0 <= t < T).  Two compile-time cases spare the per-element
+  // division by NS: if NS divides T, j / NS = t / NS + q T / NS and j mod NS = t mod NS for every
+  // q; if NS >= T E / R, every j is below NS (j / NS = 0, j mod NS = j).
+  template <int R, int NS>
+  __device__ __forceinline__ static unsigned j_mod(unsigned t, int q) {
+    if constexpr (T % NS == 0) return t % NS;
+    else if constexpr (NS >= T * (E / R)) return t + T * q;
+    else return (t + T * q) % NS;
+  }
+
   // twiddle and in-register DFT of every butterfly this thread owns (butterfly j = t + T q,
   // inputs v[q R + r] = x[j + r N/R]), for a stage of radix R after NS points were combined
   template <int R, int NS>
@@ -210,11 +220,10 @@ struct Stockham {
 #pragma unroll
     for (int q = 0; q < E / R; ++q) {
       if constexpr (NS > 1) {
-        const int jj = (t + T * q) % NS;
+        const unsigned jj = j_mod<R, NS>((unsigned)t, q);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const int e = jj * r * (N / (NS * R));
-          float2 w = __ldg(tw + e * TWS);
+          float2 w = __ldg(tw + jj * (r * (N / (NS * R)) * TWS));
           if (INV) w.y = -w.y;
           v[q * R + r] = c_mul(v[q * R + r], w);
         }
@@ -223,9 +232,18 @@ struct Stockham {
     }
   }
 
+  // output position of element r of butterfly j = t + T q
   template <int R, int NS>
-  __device__ __forceinline__ static int out_index(int j, int r) {
-    return (j / NS) * NS * R + (j % NS) + r * NS;
+  __device__ __forceinline__ static int out_index(int t, int q, int r) {
+    if constexpr (T % NS == 0) {
+      const unsigned ut = (unsigned)t;
+      return (int)((ut / NS) * (NS * R) + ut % NS) + q * (T * R) + r * NS;
+    } else if constexpr (NS >= T * (E / R)) {
+      return t + T * q + r * NS;
+    } else {
+      const int j = t + T * q;
+      return (j / NS) * NS * R + (j % NS) + r * NS;
+    }
   }
 
   // Run the stages NS.. of the radix list.  v holds the inputs of the first listed stage.
@@ -241,13 +259,13 @@ struct Stockham {
 #pragma unroll
       for (int q = 0; q < E / R; ++q)
 #pragma unroll
-        for (int r = 0; r < R; ++r) store(out_index<R, NS>(t + T * q, r), v[q * R + r]);
+        for (int r = 0; r < R; ++r) store(out_index<R, NS>(t, q, r), v[q * R + r]);
     } else {
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < E / R; ++q)
 #pragma unroll
-        for (int r = 0; r < R; ++r) mem(out_index<R, NS>(t + T * q, r)) = v[q * R + r];
+        for (int r = 0; r < R; ++r) mem(out_index<R, NS>(t, q, r)) = v[q * R + r];
       __syncthreads();
       constexpr int R2 = FirstRadix<Radices<Rest...>>::value;
 #pragma unroll

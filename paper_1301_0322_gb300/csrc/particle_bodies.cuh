@@ -8,14 +8,14 @@
 
 namespace cola {
 
-// key = ((tz_tile * nty) + ty_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
+// key = tile_bin(ty_tile, tz_tile) * 4 + ry + 2 rz, where ry (rz) marks a particle whose cell
 // is the last row of its tile along y (z): its cloud also reaches the next tile.
 // Tile sizes are powers of two (4 x 2 rows for a plan, 2 .. 16 rows per axis in an ensemble).
 __device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
   const int ty = cy >> (__ffs(tl.ty) - 1), tz = cz >> (__ffs(tl.tz) - 1);
   const int ry = ((cy & (tl.ty - 1)) == tl.ty - 1) ? 1 : 0;
   const int rz = ((cz & (tl.tz - 1)) == tl.tz - 1) ? 2 : 0;
-  return (tz * tl.nty + ty) * 4 + ry + rz;
+  return tile_bin(tl, ty, tz) * 4 + ry + rz;
 }
 
 // Bin key of particle p (plus bin_base) into keys[p]; counts[key] += 1 with one atomic per

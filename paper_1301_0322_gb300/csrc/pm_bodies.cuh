@@ -29,6 +29,13 @@ __host__ __device__ constexpr int col_width() {
   return FFTConf<N>::T * 16 <= 256 ? 16 : (FFTConf<N>::T * 8 <= 256 ? 8 : (FFTConf<N>::T * 4 <= 512 ? 4 : 2));
 }
 
+// row pitch (complex entries) of a half spectrum of an N^3 mesh: N/2 + 1 rounded up to a multiple
+// of 4 (32-byte rows, the alignment the bulk copies need)
+template <int N>
+__host__ __device__ constexpr int half_pitch() {
+  return ((N / 2 + 1) + 3) / 4 * 4;
+}
+
 // block (bx, slab): W columns of one slab of the in-place strided FFT (T(N) * W threads);
 // smem: N W float2.  Element (n, col) at data[slab * slab_stride + n * row_stride + col].
 template <int N, int W, bool INV, class C = FFTConf<N>>
@@ -60,7 +67,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   int* rbeg = ints;
   int* rpre = ints + 9;
   int* rlen = ints + 19;
-  const int tyi = tile % tl.nty, tzi = tile / tl.nty;
+  int tyi, tzi;
+  tile_of_bin(tl, tile, tyi, tzi);
   const int y0 = tyi * TY, z0 = tzi * TZ;
   for (int i = threadIdx.x; i < ROWS * N; i += NT) acc[i] = 0ull;
   // the tile's own 4 bins and the boundary bins of its 3 lower neighbours, loaded in parallel
@@ -71,7 +79,7 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
     const int ty_ = (k == 4 || k == 5 || k == 8) ? tym : tyi;
     const int tz_ = k >= 6 ? tzm : tzi;
     const int reg = k < 4 ? k : ((k == 4 || k == 5) ? (k == 4 ? 1 : 3) : (k == 6 ? 2 : 3));
-    const int b = (tz_ * tl.nty + ty_) * 4 + reg;
+    const int b = tile_bin(tl, ty_, tz_) * 4 + reg;
     const int o0 = offsets[b];
     rbeg[k] = o0;
     rlen[k] = offsets[b + 1] - o0;
@@ -279,6 +287,123 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
     };
     auto store = [&](int n, float2 x) {
       if (valid) gy[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 { return valid ? gz[(int64_t)n * P] : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) {
+      if (valid) gz[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+  }
+}
+
+// ---- 3'/4'. single-buffer (wide-strip) variants of the z and inverse y passes ------------------------------
+// For long columns the two-buffer bodies above leave room for only narrow strips (4 columns =
+// 32-byte row segments at N = 2048).  These variants keep one exchange buffer of N x W complex
+// and re-read their input strip from global memory (an L2 hit) for each transform instead of
+// holding it in shared memory, so the strips can be twice as wide.
+//
+// z pass: forward transform of the strip, phi = delta_k norm / (k^2 W(k)^p) written back to A in
+// the forward transform's last stage, then the inverse transforms of i k_z phi (-> Gz) and of phi
+// (-> A, in place).  block (bx, ky): W columns kx of the slab ky (T(N) * W threads);
+// sm: N W float2 + (N + W) floats (sinc^2 tables).
+template <int N, int W, class C = FFTConf<N>>
+__device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz, float kf,
+                                                  int deconv, float norm, const float2* __restrict__ tw, int bx,
+                                                  int ky, float2* sm) {
+  constexpr int nh = N / 2 + 1, NT = C::T * W, P = half_pitch<N>();
+  float2* S = sm;
+  float* sz2 = reinterpret_cast<float*>(sm + N * W);
+  float* sx2 = sz2 + N;
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = bx * W + w;
+  const bool valid = kx < nh;
+  constexpr int64_t zstride = (int64_t)N * P;
+  float2* a = A + (int64_t)ky * P + (valid ? kx : 0);
+  float2* gz = Gz + (int64_t)ky * P + (valid ? kx : 0);
+  for (int n = threadIdx.x; n < N + W; n += NT) {
+    const float sv = n < N ? sinc_pi_f(signed_mode(n, N), N) : sinc_pi_f(bx * W + (n - N), N);
+    (n < N ? sz2[n] : sx2[n - N]) = sv * sv;
+  }
+  __syncthreads();
+  auto mem = [&](int n) -> float2& { return S[n * W + w]; };
+  {
+    const int ny = signed_mode(ky, N);
+    const float sy = sinc_pi_f(ny, N);
+    const float wy = sy * sy;
+    const float kf2 = kf * kf;
+    auto load = [&](int n) -> float2 { return valid ? a[n * zstride] : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) {
+      const int nz = signed_mode(n, N);
+      const int m2 = kx * kx + ny * ny + nz * nz;
+      float gk = 0.0f;
+      if (m2 != 0) {
+        float den = kf2 * (float)m2;
+        if (deconv) {
+          const float wk = sx2[w] * wy * sz2[n];
+          den *= deconv == 2 ? wk * wk : wk;
+        }
+        gk = __fdividef(norm, den);
+      }
+      if (valid) a[n * zstride] = c_scale(x, gk);
+    };
+    fft_1d<N, 1, false, C>(t, tw, load, mem, store);
+  }
+  __syncthreads();  // phi of the strip is in A (global writes of this block, visible after the barrier)
+  {
+    auto load = [&](int n) -> float2 {
+      const float kz = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
+      return valid ? mul_ik(__ldcg(a + n * zstride), kz) : make_float2(0.f, 0.f);
+    };
+    auto store = [&](int n, float2 x) {
+      if (valid) gz[n * zstride] = x;
+    };
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 { return valid ? __ldcg(a + n * zstride) : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) {
+      if (valid) a[n * zstride] = x;
+    };
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+  }
+}
+
+// inverse y passes, one exchange buffer: Gy = IFFT_y(i k_y B), then B = IFFT_y(B) in place (the
+// strip of B read again, from L2), then Gz = IFFT_y(Gz).  block (bx, z): W columns kx of the slab
+// z (T(N) * W threads); sm: N W float2
+template <int N, int W, class C = FFTConf<N>>
+__device__ __forceinline__ void y_inv3_wide_body(float2* __restrict__ B, float2* __restrict__ Gy,
+                                                 float2* __restrict__ Gz, float kf, const float2* __restrict__ tw,
+                                                 int bx, int z, float2* sm) {
+  constexpr int nh = N / 2 + 1, T = C::T, P = half_pitch<N>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = bx * W + w;
+  const bool valid = kx < nh;
+  const int64_t slab = (int64_t)z * N * P + (valid ? kx : 0);
+  float2* b = B + slab;
+  float2* gy = Gy + slab;
+  float2* gz = Gz + slab;
+  // the Gz strip is read only by the third transform: start pulling it into L2 now
+  if (w == 0)
+    for (int n = t; n < N; n += T) prefetch_l2_line(Gz + (int64_t)z * N * P + bx * W + (int64_t)n * P);
+  auto mem = [&](int n) -> float2& { return sm[n * W + w]; };
+  {
+    auto load = [&](int n) -> float2 {
+      const float ky = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
+      return valid ? mul_ik(b[(int64_t)n * P], ky) : make_float2(0.f, 0.f);
+    };
+    auto store = [&](int n, float2 x) {
+      if (valid) gy[(int64_t)n * P] = x;
+    };
+    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+  }
+  {
+    auto load = [&](int n) -> float2 { return valid ? b[(int64_t)n * P] : make_float2(0.f, 0.f); };
+    auto store = [&](int n, float2 x) {
+      if (valid) b[(int64_t)n * P] = x;
     };
     fft_1d<N, 1, true, C>(t, tw, load, mem, store);
   }

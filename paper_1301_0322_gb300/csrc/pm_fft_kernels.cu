@@ -42,15 +42,56 @@ __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
   y_inv3_body<N, col_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
+// Strip width of the single-buffer (wide-strip) z, forward y and inverse y passes for long
+// columns, 0 where the two-buffer bodies are used.
+template <int N>
+__host__ __device__ constexpr int wide_width() {
+  return N == 2048 ? 8 : 0;
+}
+template <int N, int W>
+__host__ __device__ constexpr int wide_min_blocks() {
+  return FFTConf<N>::T * W >= 1024 ? 1 : 2;
+}
+
+template <int N, int W>
+__global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
+    k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float kf, int deconv, float norm,
+                       const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  z_green_wide_body<N, W>(A, Gz, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
+}
+
+template <int N, int W>
+__global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
+    k_fft_y_inv3_wide(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz, float kf,
+                      const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  y_inv3_wide_body<N, W>(B, Gy, Gz, kf, tw, blockIdx.x, blockIdx.y, sm);
+}
+
+// forward y pass of the half spectrum in strips of W columns (slab = z)
+template <int N, int W>
+__global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
+    k_fft_y_fwd_wide(float2* __restrict__ A, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  constexpr int P = half_pitch<N>();
+  cols_body<N, W, false>(A, (int64_t)N * P, P, N / 2 + 1, tw, blockIdx.x, blockIdx.y, sm);
+}
+
 // Persistent: each block walks items blockIdx.x, blockIdx.x + gridDim.x, ... with the bulk
-// copy of the next item in flight during the transform of the current one (double buffer).
+// copies of its next NB - 1 items in flight during the transform of the current one (NB buffers).
+template <int N>
+__host__ __device__ constexpr int c2r3_stages() {
+  return 2;
+}
+
 template <int N>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 3)
     k_fft_x_c2r3(const float2* __restrict__ C, const float2* __restrict__ Gy, const float2* __restrict__ Gz,
                  float* __restrict__ F, int P, float kf, const float2* __restrict__ tw, int* __restrict__ err) {
-  constexpr int M = N / 2, RB = c2r3_rows<N>(), LD = xrow_ld<M>();
+  constexpr int M = N / 2, RB = c2r3_rows<N>(), LD = xrow_ld<M>(), NB = c2r3_stages<N>();
   extern __shared__ __align__(128) float2 c2r_stage[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[NB];
   const int64_t nrb = (int64_t)N * N / RB, total = 3 * nrb;
   auto src_of = [&](int64_t item) -> const float2* {
     const int comp = (int)(item / nrb);
@@ -58,24 +99,28 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 3)
     return m + (item - comp * nrb) * RB * P;
   };
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int k = 0; k < NB; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
   }
   __syncthreads();
+  // prologue: the first NB - 1 items
+  for (int k = 0; k < NB - 1; ++k) {
+    const int64_t item = blockIdx.x + (int64_t)k * gridDim.x;
+    if (item < total && threadIdx.x < 32) c2r3_issue(c2r_stage + k * RB * LD, src_of(item), RB, P, LD, &bars[k]);
+  }
   int64_t item = blockIdx.x;
-  if (item < total && threadIdx.x < 32) c2r3_issue(c2r_stage, src_of(item), RB, P, LD, &bars[0]);
   for (int it = 0; item < total; ++it, item += gridDim.x) {
-    const int b = it & 1;
-    const int64_t next = item + gridDim.x;
-    if (next < total && threadIdx.x < 32) c2r3_issue(c2r_stage + (b ^ 1) * RB * LD, src_of(next), RB, P, LD, &bars[b ^ 1]);
-    const bool ok = mbar_wait(&bars[b], (it >> 1) & 1);
+    const int b = it % NB;
+    const int64_t ahead = item + (int64_t)(NB - 1) * gridDim.x;
+    const int ba = (it + NB - 1) % NB;  // consumed at iteration it - 1, free after its closing barrier
+    if (ahead < total && threadIdx.x < 32) c2r3_issue(c2r_stage + ba * RB * LD, src_of(ahead), RB, P, LD, &bars[ba]);
+    const bool ok = mbar_wait(&bars[b], (it / NB) & 1);
     if (__syncthreads_or(!ok)) {
       // leave no bulk copy in flight into shared memory the block releases: wait again (bounded)
-      // for the copy that timed out and for the next item's copy
+      // for the copy that timed out and for every later one already issued
       if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
-      mbar_wait(&bars[b], (it >> 1) & 1);
-      if (next < total) mbar_wait(&bars[b ^ 1], ((it + 1) >> 1) & 1);
+      for (int k = 0; k < NB; ++k)
+        if (item + (int64_t)k * gridDim.x < total) mbar_wait(&bars[(it + k) % NB], ((it + k) / NB) & 1);
       return;
     }
     const int comp = (int)(item / nrb);
@@ -96,10 +141,11 @@ static int set_smem(K kernel, size_t bytes) {
 
 template <int N>
 static const char* flabel(int kind) {
-  static const std::string names[4] = {std::string("deposit_fftx_") + std::to_string(N),
+  static const std::string names[5] = {std::string("deposit_fftx_") + std::to_string(N),
                                        std::string("fft_z_green_") + std::to_string(N),
                                        std::string("fft_y_inv3_") + std::to_string(N),
-                                       std::string("fft_x_c2r3_") + std::to_string(N)};
+                                       std::string("fft_x_c2r3_") + std::to_string(N),
+                                       std::string("fft_cols_fwd_") + std::to_string(N)};
   return names[kind].c_str();
 }
 
@@ -132,6 +178,36 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     }
     COLA_LAUNCH_CHECK();
   }
+  constexpr int WW = wide_width<N>();
+  if constexpr (WW > 0) {
+    if (P != half_pitch<N>()) return fail(COLA_EINVAL, "wide column passes: unexpected half-spectrum pitch");
+    const dim3 grid((nh + WW - 1) / WW, N);
+    constexpr int NT = FFTConf<N>::T * WW;
+    // 2. forward y pass
+    {
+      const size_t smem = sizeof(float2) * N * WW;
+      if ((rc = set_smem(k_fft_y_fwd_wide<N, WW>, smem))) return rc;
+      LaunchScope ls_(flabel<N>(4), st);
+      k_fft_y_fwd_wide<N, WW><<<grid, NT, smem, st>>>(A, tw);
+      COLA_LAUNCH_CHECK();
+    }
+    // 3. z pass with the Green's function
+    {
+      const size_t smem = sizeof(float2) * N * WW + sizeof(float) * (N + WW);
+      if ((rc = set_smem(k_fft_z_green_wide<N, WW>, smem))) return rc;
+      LaunchScope ls_(flabel<N>(1), st);
+      k_fft_z_green_wide<N, WW><<<grid, NT, smem, st>>>(A, Gz, kf, deconv, norm, tw);
+      COLA_LAUNCH_CHECK();
+    }
+    // 4. inverse y passes
+    {
+      const size_t smem = sizeof(float2) * N * WW;
+      if ((rc = set_smem(k_fft_y_inv3_wide<N, WW>, smem))) return rc;
+      LaunchScope ls_(flabel<N>(2), st);
+      k_fft_y_inv3_wide<N, WW><<<grid, NT, smem, st>>>(A, Gy, Gz, kf, tw);
+      COLA_LAUNCH_CHECK();
+    }
+  } else {
   // 2. forward y pass
   if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
   // 3. z pass with the Green's function
@@ -152,10 +228,11 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     k_fft_y_inv3<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gy, Gz, P, kf, tw);
     COLA_LAUNCH_CHECK();
   }
+  }
   // 5. inverse x passes (persistent, bulk-copy pipelined)
   {
     constexpr int RB = c2r3_rows<N>(), T = FFTConf<M>::T;
-    const size_t smem = sizeof(float2) * 2 * RB * xrow_ld<M>();
+    const size_t smem = sizeof(float2) * c2r3_stages<N>() * RB * xrow_ld<M>();
     if ((rc = set_smem(k_fft_x_c2r3<N>, smem))) return rc;
     const int64_t nrows = (int64_t)N * N;
     if (nrows % RB) return fail(COLA_EINVAL, "fused c2r: row count not a multiple of the block rows");

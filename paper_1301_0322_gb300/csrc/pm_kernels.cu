@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uin
   extern __shared__ unsigned long long acc[];
   __shared__ int rbeg[9], rpre[10];
   const int ng = g.ng;
-  const int tyi = blockIdx.x % tl.nty, tzi = blockIdx.x / tl.nty;
+  int tyi, tzi;
+  tile_of_bin(tl, blockIdx.x, tyi, tzi);
   const int y0 = tyi * TY, z0 = tzi * TZ;
   const int ncell = TZ * TY * ng;
   for (int i = threadIdx.x; i < ncell; i += blockDim.x) acc[i] = 0ull;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) k_deposit(Geometry g, Tiles tl, const uin
     const int reg[9] = {0, 1, 2, 3, 1, 3, 2, 3, 3};
     int run = 0;
     for (int k = 0; k < 9; ++k) {
-      const int b = (tzs[k] * tl.nty + tys[k]) * 4 + reg[k];
+      const int b = tile_bin(tl, tys[k], tzs[k]) * 4 + reg[k];
       rbeg[k] = offsets[b];
       rpre[k] = run;
       run += offsets[b + 1] - offsets[b];
