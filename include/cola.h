@@ -238,12 +238,15 @@ int cola_status(cola_plan* plan, cola_stream stream);
  * Same result as cola_power on a plan with this ng and box: P(k) of the float32 density
  * delta [ng^3] in shells b = 1..nbins, written to the caller's device arrays k, pk (float64)
  * and nmodes (int64).  Its scratch is one static device array sized for ng <= 128 (about
- * 9.8 MiB held on every GPU that loads the library until the process exits); ng > 128 is
- * rejected with COLA_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture on the device.  Every call shares the one
- * array and leaves its contents behind (each call overwrites every partial sum it reads), so calls that overlap on the GPU -- on different streams or from different
- * threads -- race and must be serialised by the caller. */
+ * 10.7 MiB held on every GPU that loads the library until the process exits); ng > 128 is
+ * rejected with COLA_EINVAL, sizes other than 32, 48, 64, 96 and 128 with COLA_EUNSUPPORTED.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), and the first call for each
+ * mesh size on a device uploads that size's twiddle table into the array (a synchronous copy);
+ * make those first calls before any stream capture on the device.  Every call shares the one
+ * array and leaves its contents behind (each call overwrites every partial sum it reads), so
+ * calls that overlap on the GPU -- on different streams or from different threads -- race and
+ * must be serialised by the caller. */
 #define COLA_NOALLOC_MAX_NG 128
 int cola_power_noalloc(const float* delta, int32_t ng, double box, int32_t nbins, double* k, double* pk,
                        int64_t* nmodes, cola_stream stream);

@@ -204,6 +204,8 @@ int launch_ic_adjoint_product(int64_t n3, const float* a, const float* b, const 
 // blocks of the binning kernel (fixed, so that the per-block partial sums and their reduction
 // order, hence the result, do not depend on the launch)
 constexpr int kPowerBlocks = 456;  // 3 blocks per SM of 152
+// partial sums per block and shell: 3 (k, P, modes) for P(k), 5 for the cross spectrum
+constexpr int kPowerQuantities = 5;
 int power_partial_doubles(int nbins);  // size of the partial-sum buffer
 int launch_power_bin(int ng, int P, double box, int nbins, const float2* dk, double* partial, cudaStream_t st);
 int launch_power_finish(int nbins, const double* partial, double* k, double* pk, int64_t* nmodes, cudaStream_t st);

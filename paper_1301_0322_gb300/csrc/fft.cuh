@@ -190,9 +190,18 @@ struct FirstRadix<Radices<R0, Rs...>> {
   static constexpr int value = R0;
 };
 
-// padded index of the row-layout exchange buffers (one pad slot per 8 entries: the stride-R
-// stores of the first Stockham stages then fall on distinct banks); row pitch = 8 mod 16
-__device__ __forceinline__ int xpad(int n) { return n + (n >> 3); }
+// padded index of the row-layout exchange buffers: the first Stockham stage stores with stride
+// R0 (its radix) between consecutive threads, so one pad slot per R0 entries (per 8 for R0 <= 8)
+// puts those stores on distinct banks (row pitch xrow_ld, 8 mod 16, leaves room for either)
+template <int R0>
+__device__ __forceinline__ int xpad(int n) {
+  constexpr int shift = R0 >= 16 ? 4 : 3;
+  return n + (n >> shift);
+}
+template <class C>
+__host__ __device__ constexpr int first_radix() {
+  return FirstRadix<typename C::radices>::value;
+}
 template <int M>
 __host__ __device__ constexpr int xrow_ld() {
   return ((M + 1 + ((M + 1) >> 3) + 1) + 15) / 16 * 16 + 8;

@@ -15,13 +15,25 @@ __host__ __device__ constexpr int x_rows() {
   return FFTConf<N / 2>::T >= 256 ? 1 : 256 / FFTConf<N / 2>::T;
 }
 
+// Columns per block of the stand-alone column passes: 8 (64-byte row segments) for the 16-element
+// transforms of length 1024 and 2048, whose one exchange buffer leaves room for them (the
+// two-buffer force passes at those lengths use col_width).
+template <int N>
+__host__ __device__ constexpr int cols_pass_width() {
+  return (N == 1024 || N == 2048) ? 8 : col_width<N>();
+}
+template <int N>
+__host__ __device__ constexpr int cols_pass_min_blocks() {
+  return FFTConf<N>::T * cols_pass_width<N>() >= 1024 ? 1 : 2;
+}
+
 // In-place FFT of ncols columns per slab: element (n, col) at data[slab*slab_stride + n*row_stride + col].
 template <int N, bool INV>
-__global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
+__global__ void __launch_bounds__(FFTConf<N>::T * cols_pass_width<N>(), cols_pass_min_blocks<N>())
     k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols,
                const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
-  cols_body<N, col_width<N>(), INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
+  cols_body<N, cols_pass_width<N>(), INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
 }
 
 // Real rows of length N -> half-spectrum rows (N/2 + 1 entries, stride P), via a complex
@@ -31,21 +43,22 @@ template <int N>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
     k_fft_x_r2c(const float* __restrict__ in, float2* __restrict__ out, int P, const float2* __restrict__ tw) {
   constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
+  constexpr int R0 = first_radix<FFTConf<M>>();
   extern __shared__ float2 smem[];
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = reinterpret_cast<const float2*>(in + row * N);
   float2* buf = smem + w * LD;
   auto load = [&](int n) -> float2 { return src[n]; };
-  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
-  auto store = [&](int n, float2 x) { buf[xpad(n)] = x; };
+  auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
+  auto store = [&](int n, float2 x) { buf[xpad<R0>(n)] = x; };
   fft_1d<M, 2, false>(t, tw, load, mem, store);
   __syncthreads();
   float2* dst = out + row * P;
   // X[k] = e + p and X[M - k] = conj(e - p) from one pair Z[k], Z[M - k] (p = W^k (-i d))
   for (int k = t; k <= M / 2; k += T) {
-    const float2 a = buf[xpad(k)];
-    const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
+    const float2 a = buf[xpad<R0>(k)];
+    const float2 b = c_conj(buf[xpad<R0>(k == 0 ? 0 : M - k)]);
     const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
     const float2 d = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
     const float2 p = c_mul(__ldg(tw + k), make_float2(d.y, -d.x));
@@ -60,20 +73,21 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
     k_fft_x_c2r(const float2* __restrict__ in, float* __restrict__ out, int P, const float2* __restrict__ tw,
                 float scale) {
   constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
+  constexpr int R0 = first_radix<FFTConf<M>>();
   extern __shared__ float2 smem[];
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = in + row * P;
   float2* buf = smem + w * LD;
-  for (int k = t; k <= M; k += T) buf[xpad(k)] = src[k];
+  for (int k = t; k <= M; k += T) buf[xpad<R0>(k)] = src[k];
   __syncthreads();
   auto load = [&](int n) -> float2 {
-    const float2 a = buf[xpad(n)], b = c_conj(buf[xpad(M - n)]);
+    const float2 a = buf[xpad<R0>(n)], b = c_conj(buf[xpad<R0>(M - n)]);
     const float2 e = c_add(a, b);
     const float2 o = c_mul(c_sub(a, b), c_conj(__ldg(tw + n)));
     return make_float2(e.x - o.y, e.y + o.x);  // e + i o
   };
-  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
+  auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   float2* dst = reinterpret_cast<float2*>(out + row * N);
   auto store = [&](int n, float2 x) { dst[n] = c_scale(x, scale); };
   fft_1d<M, 2, true>(t, tw, load, mem, store);
@@ -122,7 +136,7 @@ static int x_c2r(const float2* in, float* out, int64_t nrows, int P, const float
 template <int N>
 static int cols(bool inverse, float2* data, int64_t nslabs, int64_t slab_stride, int64_t row_stride, int ncols,
                 const float2* tw, cudaStream_t st) {
-  constexpr int W = col_width<N>();
+  constexpr int W = cols_pass_width<N>();
   const size_t smem = (size_t)N * W * sizeof(float2);
   if (nslabs > 65535) return fail(COLA_EINVAL, "fft column pass: too many slabs");
   dim3 grid((ncols + W - 1) / W, (unsigned)nslabs);

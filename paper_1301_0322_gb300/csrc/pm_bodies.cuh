@@ -63,7 +63,7 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
                                                   const int* __restrict__ offsets, float2* __restrict__ out, int P,
                                                   const float2* __restrict__ tw, float dscale, int* __restrict__ err,
                                                   int tile, unsigned long long* acc, int* ints) {
-  constexpr int M = N / 2, T = CM::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS;
+  constexpr int M = N / 2, T = CM::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS, R0 = first_radix<CM>();
   int* rbeg = ints;
   int* rpre = ints + 9;
   int* rlen = ints + 19;
@@ -158,8 +158,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
     const unsigned long long b = ((unsigned long long)h.y << 32) | l.y;
     return make_float2(fmaf(__ull2float_rn(a), dscale, -1.0f), fmaf(__ull2float_rn(b), dscale, -1.0f));
   };
-  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
-  auto store = [&](int n, float2 x) { buf[xpad(n)] = x; };
+  auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
+  auto store = [&](int n, float2 x) { buf[xpad<R0>(n)] = x; };
   fft_1d<M, 2, false, CM>(t, tw, load, mem, store);
   if (overflow) atomicOr(err, kErrOverflow);
   __syncthreads();
@@ -169,8 +169,8 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   // d = (Z[k] - conj Z[M - k]) / 2 and p = W^k (-i d), X[k] = e + p and X[M - k] = conj(e - p)
   // (as W^(M - k) = -conj W^k); k = 0 gives X[0] and X[M] from Z[0]
   for (int k = t; k <= M / 2; k += T) {
-    const float2 a = buf[xpad(k)];
-    const float2 b = c_conj(buf[xpad(k == 0 ? 0 : M - k)]);
+    const float2 a = buf[xpad<R0>(k)];
+    const float2 b = c_conj(buf[xpad<R0>(k == 0 ? 0 : M - k)]);
     const float2 e = c_scale(c_add(a, b), 0.5f);
     const float2 d = c_scale(c_sub(a, b), 0.5f);
     const float2 p = c_mul(__ldg(tw + k), make_float2(d.y, -d.x));
@@ -441,7 +441,7 @@ __device__ __forceinline__ void c2r3_issue(float2* stage, const float2* src_rows
 template <int N, int RB, class CM = FFTConf<N / 2>>
 __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ Frows, int comp, float kf,
                                              const float2* __restrict__ tw) {
-  constexpr int M = N / 2, T = CM::T, LD = xrow_ld<M>();
+  constexpr int M = N / 2, T = CM::T, LD = xrow_ld<M>(), R0 = first_radix<CM>();
   static_assert(T * RB <= 1024, "block too large");
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   float2* buf = stage + w * LD;
@@ -455,7 +455,7 @@ __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ 
     const float2 o = c_mul(c_sub(a, bb), c_conj(__ldg(tw + n)));
     return make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
   };
-  auto mem = [&](int n) -> float2& { return buf[xpad(n)]; };
+  auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   float2* dst = reinterpret_cast<float2*>(Frows + (int64_t)w * N);
   auto store = [&](int n, float2 x) { dst[n] = x; };
   fft_1d<M, 2, true, CM>(t, tw, load, mem, store);

@@ -34,6 +34,7 @@ template <int NF>
 __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, const float2* __restrict__ dk,
                             const float2* __restrict__ dk2, double* __restrict__ partial) {
   constexpr int NQ = NF == 1 ? 3 : 5;
+  static_assert(NQ <= kPowerQuantities, "partial sums beyond the sized buffers");
   extern __shared__ double pacc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nh = ng / 2 + 1;
@@ -180,12 +181,13 @@ static int power_warps(int nbins, int nq) {
   return std::max(1, std::min(8, w));
 }
 
-int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * 5; }
+int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * kPowerQuantities; }
 
 template <int NF>
 static int power_bin_t(int ng, int P, double box, int nbins, const float2* dk, const float2* dk2, double* partial,
                        cudaStream_t st) {
   constexpr int NQ = NF == 1 ? 3 : 5;
+  static_assert(NQ <= kPowerQuantities, "partial sums beyond the sized buffers");
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const double ng6 = std::pow((double)ng, 6.0);
   const float pnorm = (float)(box * box * box / ng6);

@@ -26,11 +26,12 @@ def cola():
     return c
 
 
-@pytest.mark.parametrize("ng,box", [(64, 100.0), (128, 250.0)])
-def test_noalloc_power_matches_plan_power_on_consecutive_calls(cola, ng, box):
+@pytest.mark.parametrize("ng,box,nbins", [(32, 50.0, 16), (64, 100.0, 32), (96, 150.0, 48), (128, 250.0, 64),
+                                         (128, 250.0, 128)])
+def test_noalloc_power_matches_plan_power_on_consecutive_calls(cola, ng, box, nbins):
+    # nbins = ng fills the shell-sum region up to its bound
     from paper_1301_0322_gb300.cola import cola_power_noalloc
     plan = cola.Plan(np_side=32, ng=ng, box=box)
-    nbins = ng // 2
     for call in range(2):
         d = torch.from_numpy(inputs.gaussian_noise(ng, 40 + call) * (0.3 + call)).cuda()
         k_ref, p_ref, n_ref = (t.cpu().numpy() for t in plan.power(d, nbins))
