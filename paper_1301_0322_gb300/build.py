@@ -14,7 +14,8 @@ LIB = os.path.join(HERE, "libcola_gb300.so")
 SOURCES = ["api.cu", "coeffs.cpp", "fft_kernels.cu", "pm_kernels.cu", "ic_kernels.cu", "power_kernels.cu",
            "power_noalloc.cu", "pm_fft_kernels.cu", "adjoint_kernels.cu", "ensemble.cu",
            "fof.cu"]
-HEADERS = ["cola_internal.cuh", "fft.cuh", "pm_common.cuh", "profiler.cuh", "pm_bodies.cuh", "particle_bodies.cuh"]
+HEADERS = ["cola_internal.cuh", "fft.cuh", "pm_common.cuh", "profiler.cuh", "pm_bodies.cuh", "particle_bodies.cuh",
+           "tma.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH

@@ -258,19 +258,26 @@ struct Stockham {
   // Run the stages NS.. of the radix list.  v holds the inputs of the first listed stage.
   // mem(n) -> float2& : exchange buffer slot for element n of this thread's sequence.
   // store(n, x)       : final output of element n.
-  template <int NS, int R, int... Rest, class Mem, class Store>
+  // before() / after(): called by every thread just before / after the first block barrier,
+  // the one that separates the first stage's reads of its inputs from the first exchange
+  // writes (a block that reads its inputs from a buffer may hand the buffer on after it).
+  template <int NS, int R, int... Rest, class Mem, class Store, class Before, class After>
   __device__ __forceinline__ static void run(float2 (&v)[E], int t, const float2* __restrict__ tw,
-                                             Mem& mem, Store& store) {
+                                             Mem& mem, Store& store, Before& before, After& after) {
     compute<R, NS>(v, t, tw);
     if constexpr (sizeof...(Rest) == 0) {
       static_assert(NS * R == N, "radix list does not multiply to N");
+      if constexpr (NS == 1) before();
       __syncthreads();
+      if constexpr (NS == 1) after();
 #pragma unroll
       for (int q = 0; q < E / R; ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r) store(out_index<R, NS>(t, q, r), v[q * R + r]);
     } else {
+      if constexpr (NS == 1) before();
       __syncthreads();
+      if constexpr (NS == 1) after();
 #pragma unroll
       for (int q = 0; q < E / R; ++q)
 #pragma unroll
@@ -281,20 +288,24 @@ struct Stockham {
       for (int q = 0; q < E / R2; ++q)
 #pragma unroll
         for (int r = 0; r < R2; ++r) v[q * R2 + r] = mem(t + T * q + r * (N / R2));
-      run<NS * R, Rest...>(v, t, tw, mem, store);
+      run<NS * R, Rest...>(v, t, tw, mem, store, before, after);
     }
   }
 
-  template <int... Rs, class Mem, class Store>
+  template <int... Rs, class Mem, class Store, class Before, class After>
   __device__ __forceinline__ static void run_all(Radices<Rs...>, float2 (&v)[E], int t,
-                                                 const float2* __restrict__ tw, Mem& mem, Store& store) {
-    run<1, Rs...>(v, t, tw, mem, store);
+                                                 const float2* __restrict__ tw, Mem& mem, Store& store,
+                                                 Before& before, After& after) {
+    run<1, Rs...>(v, t, tw, mem, store, before, after);
   }
 };
 
-// Convenience wrapper: load the first-stage inputs with load(n) and run the whole transform.
-template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store>
-__device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Load& load, Mem& mem, Store& store) {
+// Convenience wrapper: load the first-stage inputs with load(n) and run the whole transform,
+// with before() / after() around the first block barrier (see Stockham::run).
+template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store, class Before,
+          class After>
+__device__ __forceinline__ void fft_1d_hooked(int t, const float2* __restrict__ tw, Load& load, Mem& mem,
+                                              Store& store, Before& before, After& after) {
   static_assert(C::N == N, "configuration of another length");
   constexpr int E = C::E, T = C::T;
   constexpr int R0 = FirstRadix<typename C::radices>::value;
@@ -303,7 +314,13 @@ __device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Loa
   for (int q = 0; q < E / R0; ++q)
 #pragma unroll
     for (int r = 0; r < R0; ++r) v[q * R0 + r] = load(t + T * q + r * (N / R0));
-  Stockham<N, E, TWS, INV>::run_all(typename C::radices{}, v, t, tw, mem, store);
+  Stockham<N, E, TWS, INV>::run_all(typename C::radices{}, v, t, tw, mem, store, before, after);
+}
+
+template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store>
+__device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Load& load, Mem& mem, Store& store) {
+  auto none = [] {};
+  fft_1d_hooked<N, TWS, INV, C>(t, tw, load, mem, store, none, none);
 }
 
 }  // namespace cola

@@ -16,8 +16,15 @@
 namespace cola {
 
 // ---- single-box kernels ------------------------------------------------------------------------
+// resident blocks per SM the fused deposit is compiled for: 512 threads per SM, and three blocks
+// of 2 x 2 tiles at N = 2048 (64 KB of cell sums each; 80 registers, no spills)
 template <int N, int TY, int TZ>
-__global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, (512 / (FFTConf<N / 2>::T * TY * TZ)) > 0 ? 512 / (FFTConf<N / 2>::T * TY * TZ) : 1)
+__host__ __device__ constexpr int deposit_min_blocks() {
+  return N == 2048 && TY * TZ == 4 ? 3 : ((512 / (FFTConf<N / 2>::T * TY * TZ)) > 0 ? 512 / (FFTConf<N / 2>::T * TY * TZ) : 1);
+}
+
+template <int N, int TY, int TZ>
+__global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, deposit_min_blocks<N, TY, TZ>())
     k_deposit_fftx(Geometry g, Tiles tl, const uint4* __restrict__ rec, const int* __restrict__ offsets,
                    float2* __restrict__ out, int P, const float2* __restrict__ tw, float dscale,
                    int* __restrict__ err) {
@@ -85,8 +92,15 @@ __host__ __device__ constexpr int c2r3_stages() {
   return 2;
 }
 
+// resident blocks per SM of the inverse-x pass: four at N = 2048 (128 registers, no spills;
+// 16 warps to cover the shared-memory latency of the staged rows), three otherwise
 template <int N>
-__global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), 3)
+__host__ __device__ constexpr int c2r3_min_blocks() {
+  return N == 2048 ? 4 : 3;
+}
+
+template <int N>
+__global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), c2r3_min_blocks<N>())
     k_fft_x_c2r3(const float2* __restrict__ C, const float2* __restrict__ Gy, const float2* __restrict__ Gz,
                  float* __restrict__ F, int P, float kf, const float2* __restrict__ tw, int* __restrict__ err) {
   constexpr int M = N / 2, RB = c2r3_rows<N>(), LD = xrow_ld<M>(), NB = c2r3_stages<N>();
