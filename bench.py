@@ -161,7 +161,9 @@ def algorithmic_bytes(name, n_p, ng):
         "kspace_force": 4 * 8 * ng * ng * (ng // 2 + 1),
         "gather_kick_drift": 72 * np3 + 12 * ng3,  # s, v, s1, s2 in, s, v out; 3 force meshes once
         "gather_binned": 28 * np3 + 12 * ng3,  # index + coordinates in, force out; 3 force meshes once
+        "gather_binned4": 32 * np3 + 12 * ng3,  # the same with the force as one float4 per particle
         "kick_drift": 84 * np3,            # force, s, v, s1, s2 in; s, v out
+        "kick_drift4": 88 * np3,           # the same with the force read as one float4
         "keys": 16 * np3,
         "scatter": 32 * np3,               # key + displacement in; index + fixed-point coordinates out
         "power_bin": 8 * ng * ng * (ng // 2 + 1),
@@ -269,7 +271,8 @@ def reference_arm(args):
 # ---- the GB300 arm ------------------------------------------------------------------------------------
 # kernels of one force evaluation (binning, mesh passes, gather, kick/drift) by profiler label
 EVAL_KERNELS = ("keys", "scan_reduce", "scan_blocks", "scan_apply", "scatter", "deposit_fftx_", "fft_cols_fwd_",
-                "fft_z_green_", "fft_y_inv3_", "fft_x_c2r3_", "gather_binned", "kick_drift", "gather_kick_drift")
+                "fft_z_green_", "fft_y_inv3_", "fft_x_c2r3_", "gather_binned", "kick_drift", "gather_kick_drift",
+                "gather_binned4", "kick_drift4")
 
 
 def eval_floor_bytes(n_p, ng):

@@ -198,6 +198,7 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   p->Pg = padded_half((int)c.ng);
   p->Pp = padded_half((int)c.np);
   p->binned_gather = (double)sizeof(float2) * c.ng * c.ng * p->Pg >= (double)sizeof(float) * p->geo.np3;
+  p->binned_gather4 = (double)sizeof(float2) * c.ng * c.ng * p->Pg >= (double)sizeof(float4) * p->geo.np3;
   std::string why;
   int rc = build_coefficients(c, p->coef64, p->pk_amp, p->d2u1, why);
   if (rc) {
@@ -332,6 +333,11 @@ int cola_step(cola_plan* plan, int32_t step, float* s, float* v, const float* s1
   if (!plan->binned_gather)
     return launch_gather_kick_drift(plan->geo, w.freal, s, v, s1, s2, coef, mode, nullptr, st);
   // the gathered forces go to the half-spectrum buffers, free once the force meshes exist
+  if (plan->binned_gather4) {
+    float4* f4 = reinterpret_cast<float4*>(w.meshA);
+    if ((rc = launch_gather_binned4(plan->geo, w.freal, w.rec, f4, st))) return rc;
+    return launch_kick_drift4(plan->geo, f4, s, v, s1, s2, coef, mode, st);
+  }
   float* f[3] = {reinterpret_cast<float*>(w.meshA), reinterpret_cast<float*>(w.meshG[1]),
                  reinterpret_cast<float*>(w.meshG[2])};
   if ((rc = launch_gather_binned(plan->geo, w.freal, w.rec, f[0], f[1], f[2], st))) return rc;

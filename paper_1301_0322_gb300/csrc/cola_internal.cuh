@@ -102,8 +102,10 @@ struct cola_plan {
   cola::Tiles tiles;
   int Pg = 0, Pp = 0;  // padded half-spectrum row lengths (complex) for ng and np
   int64_t ng3 = 0;
-  // the step gathers in bin order into the half-spectrum buffers (each holds np^3 floats)
+  // the step gathers in bin order into the half-spectrum buffers (each holds np^3 floats), as
+  // one float4 per particle into the first of them when it holds 16 bytes per particle
   bool binned_gather = false;
+  bool binned_gather4 = false;
   // retry limit of the friends-of-friends union-find (cola_set_fof_union_tries)
   int fof_union_tries = 1 << 20;
   std::vector<double> coef64;
@@ -171,6 +173,11 @@ int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec
                          float* f0, float* f1, float* f2, cudaStream_t st);
 int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,
                       const float* s1, const float* s2, const float* coef_row, int mode, cudaStream_t st);
+// the same with the force of particle p as one float4 f4[p] (used when a half spectrum holds
+// 16 bytes per particle)
+int launch_gather_binned4(const Geometry& g, const float* fmesh, const uint4* rec, float4* f4, cudaStream_t st);
+int launch_kick_drift4(const Geometry& g, const float4* f4, float* s, float* v, const float* s1, const float* s2,
+                       const float* coef_row, int mode, cudaStream_t st);
 
 // IC kernels (ic_kernels.cu)
 int launch_noise(int np, uint64_t seed, float* out, cudaStream_t st);

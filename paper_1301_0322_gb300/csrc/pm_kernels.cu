@@ -250,6 +250,40 @@ __global__ void __launch_bounds__(256) k_gather_binned(Geometry g, const float* 
   f2[p] = f[2];
 }
 
+// As k_gather_binned, with the three components written as one 16-byte float4 at the particle's
+// lattice index: once the particles cluster, consecutive bin positions belong to scattered
+// lattice indices, and one 16-byte write touches one 32-byte sector where three 4-byte writes
+// to three arrays touch three.
+__global__ void __launch_bounds__(256) k_gather_binned4(Geometry g, const float* __restrict__ fmesh,
+                                                         const uint4* __restrict__ rec, float4* __restrict__ f4) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.np3) return;
+  const uint4 q = __ldg(rec + i);
+  const uint32_t fmask = (1u << g.fbits) - 1u;
+  const uint32_t fq[3] = {q.x, q.y, q.z};
+  int c[3], t[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    c[d] = (int)(fq[d] >> g.fbits);
+    t[d] = (int)(fq[d] & fmask);
+  }
+  float f[3];
+  gather_force(g, fmesh, c, t, f);
+  f4[q.w] = make_float4(f[0], f[1], f[2], 0.0f);
+}
+
+// Kick/drift in lattice order with the forces of k_gather_binned4.
+__global__ void __launch_bounds__(256) k_kick_drift4(Geometry g, const float4* __restrict__ f4,
+                                                      float* __restrict__ s, float* __restrict__ v,
+                                                      const float* __restrict__ s1, const float* __restrict__ s2,
+                                                      const float* __restrict__ coef, int mode) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np3) return;
+  const float4 q = __ldg(f4 + p);
+  const float f[3] = {q.x, q.y, q.z};
+  kick_drift_update(g, s, v, s1, s2, coef, mode, p, f);
+}
+
 // Kick/drift in lattice order with the gathered force fj[p].
 __global__ void __launch_bounds__(256) k_kick_drift(Geometry g, const float* __restrict__ f0,
                                                      const float* __restrict__ f1, const float* __restrict__ f2,
@@ -349,6 +383,21 @@ int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec
                          float* f0, float* f1, float* f2, cudaStream_t st) {
   { LaunchScope ls_("gather_binned", st);
   k_gather_binned<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, rec, f0, f1, f2); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_gather_binned4(const Geometry& g, const float* fmesh, const uint4* rec, float4* f4, cudaStream_t st) {
+  { LaunchScope ls_("gather_binned4", st);
+  k_gather_binned4<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, fmesh, rec, f4); }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+int launch_kick_drift4(const Geometry& g, const float4* f4, float* s, float* v, const float* s1, const float* s2,
+                       const float* coef_row, int mode, cudaStream_t st) {
+  { LaunchScope ls_("kick_drift4", st);
+  k_kick_drift4<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, f4, s, v, s1, s2, coef_row, mode); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
