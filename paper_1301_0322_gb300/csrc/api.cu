@@ -186,6 +186,7 @@ int cola_plan_create(const cola_config* cfg, cola_plan** out) {
   p->geo.fbits = c.fixed_bits;
   p->geo.ratio = (c.ng % c.np == 0) ? (int)(c.ng / c.np) : 0;
   p->geo.scale32 = (float)((double)c.ng / c.box);
+  set_np_divider(p->geo);
   p->ng3 = c.ng * c.ng * c.ng;
   // deposit tiles of 4 x 2 mesh rows (y, z), each spanning the whole x extent (2 x 2 at ng = 2048,
   // where a 4 x 2 tile of int64 cells fills the shared memory of an SM: two blocks per SM)

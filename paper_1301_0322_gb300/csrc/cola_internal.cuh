@@ -36,7 +36,22 @@ struct Geometry {
   int fbits;
   int ratio;      // ng / np when ng is a multiple of np, else 0
   float scale32;  // fl32(ng / L)
+  // division of a 32-bit index by np as a multiply-high and shifts (set_np_divider)
+  uint32_t np_mul;
+  int np_sh1, np_sh2;
 };
+
+// Unsigned 32-bit division by an invariant d >= 1 (Granlund & Montgomery 1994, Sec. 4): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, every n < 2^32 has
+//   n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),  t = mulhi(m, n).
+inline void set_np_divider(Geometry& g) {
+  const uint64_t d = (uint64_t)g.np;
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  g.np_mul = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  g.np_sh1 = l < 1 ? l : 1;
+  g.np_sh2 = l > 1 ? l - 1 : 0;
+}
 
 struct Tiles {
   int ty, tz;     // rows per tile along y and z (the tile spans the whole x row)

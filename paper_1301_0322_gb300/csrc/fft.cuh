@@ -11,6 +11,7 @@
 // host; stage twiddles exp(-2 pi i m / N) are read at tw[m * TWS] with NT = N * TWS.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 namespace cola {
@@ -207,6 +208,77 @@ __host__ __device__ constexpr int xrow_ld() {
   return ((M + 1 + ((M + 1) >> 3) + 1) + 15) / 16 * 16 + 8;
 }
 
+// ---- stage twiddle tables in shared memory ------------------------------------------------
+// A stage of radix R after NS combined points multiplies input r of butterfly j (0 < r < R) by
+// w^r, w = exp(-2 pi i (j mod NS) / (NS R)).  From the base table these are R - 1 scattered
+// 8-byte loads per butterfly; a block may instead copy every stage's twiddles once into shared
+// memory, butterfly by butterfly, and read them as 16-byte pairs.  Row pitch stw_pitch(R) float2
+// (an even count, 2 mod 4): eight consecutive butterflies' pair loads fall on distinct banks.
+__host__ __device__ constexpr int stw_pitch(int R) {
+  const int pairs = R / 2;  // ceil((R - 1) / 2)
+  return 2 * pairs + ((pairs % 2 == 0) ? 2 : 0);
+}
+template <int... Rs>
+__host__ __device__ constexpr int stw_offset_of(Radices<Rs...>, int ns_target) {
+  int ns = 1, off = 0;
+  for (int r : {Rs...}) {
+    if (ns == ns_target) return off;
+    if (ns > 1) off += ns * stw_pitch(r);
+    ns *= r;
+  }
+  return off;
+}
+// float2 entries of the table of configuration C
+template <class C>
+__host__ __device__ constexpr int stw_size() {
+  return stw_offset_of(typename C::radices{}, C::N);
+}
+
+// Fill the table of configuration C from the base table tw (stage twiddle m at tw[m * TWS]):
+// threads tid = 0 .. nth - 1 of the block; the first use comes after the transform's first
+// block barrier, so the fill needs no barrier of its own.
+template <int N, int TWS, int... Rs>
+__device__ __forceinline__ void stw_fill_stages(Radices<Rs...>, float2* dst, const float2* __restrict__ tw,
+                                                int tid, int nth) {
+  int ns = 1, off = 0;
+  (
+      [&] {
+        constexpr int R = Rs;
+        if (ns > 1) {
+          const int p = stw_pitch(R), cnt = ns * (R - 1), step = N / (ns * R);
+          for (int i = tid; i < cnt; i += nth) {
+            const int j = i / (R - 1), r = i - j * (R - 1) + 1;
+            dst[off + j * p + r - 1] = __ldg(tw + (int64_t)j * r * step * TWS);
+          }
+          off += ns * p;
+        }
+        ns *= R;
+      }(),
+      ...);
+}
+template <class C, int TWS>
+__device__ __forceinline__ void stw_fill(float2* dst, const float2* __restrict__ tw, int tid, int nth) {
+  stw_fill_stages<C::N, TWS>(typename C::radices{}, dst, tw, tid, nth);
+}
+
+// twiddle source reading the shared-memory table of configuration C (16-byte aligned)
+template <class C>
+struct SmemTw {
+  const float2* base;
+  template <int R, int NS, bool INV>
+  __device__ __forceinline__ void apply(unsigned j, float2* x) const {
+    constexpr int off = stw_offset_of(typename C::radices{}, NS), p = stw_pitch(R);
+    const float4* q = reinterpret_cast<const float4*>(base + off + j * p);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const float4 w2 = q[k];
+      const int r = 2 * k + 1;
+      x[r] = c_mul(x[r], make_float2(w2.x, INV ? -w2.y : w2.y));
+      if (r + 1 < R) x[r + 1] = c_mul(x[r + 1], make_float2(w2.z, INV ? -w2.w : w2.w));
+    }
+  }
+};
+
 // ---- Stockham stages --------------------------------------------------------------------
 template <int N, int E, int TWS, bool INV>
 struct Stockham {
@@ -224,17 +296,22 @@ struct Stockham {
 
   // twiddle and in-register DFT of every butterfly this thread owns (butterfly j = t + T q,
   // inputs v[q R + r] = x[j + r N/R]), for a stage of radix R after NS points were combined
-  template <int R, int NS>
-  __device__ __forceinline__ static void compute(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+  // (tw: the base table, or an SmemTw stage table)
+  template <int R, int NS, class TW>
+  __device__ __forceinline__ static void compute(float2 (&v)[E], int t, const TW& tw) {
 #pragma unroll
     for (int q = 0; q < E / R; ++q) {
       if constexpr (NS > 1) {
         const unsigned jj = j_mod<R, NS>((unsigned)t, q);
+        if constexpr (!std::is_class<TW>::value) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(tw + jj * (r * (N / (NS * R)) * TWS));
-          if (INV) w.y = -w.y;
-          v[q * R + r] = c_mul(v[q * R + r], w);
+          for (int r = 1; r < R; ++r) {
+            float2 w = __ldg(tw + jj * (r * (N / (NS * R)) * TWS));
+            if (INV) w.y = -w.y;
+            v[q * R + r] = c_mul(v[q * R + r], w);
+          }
+        } else {
+          tw.template apply<R, NS, INV>(jj, &v[q * R]);
         }
       }
       DFT<R, INV>::run(&v[q * R]);
@@ -261,9 +338,9 @@ struct Stockham {
   // before() / after(): called by every thread just before / after the first block barrier,
   // the one that separates the first stage's reads of its inputs from the first exchange
   // writes (a block that reads its inputs from a buffer may hand the buffer on after it).
-  template <int NS, int R, int... Rest, class Mem, class Store, class Before, class After>
-  __device__ __forceinline__ static void run(float2 (&v)[E], int t, const float2* __restrict__ tw,
-                                             Mem& mem, Store& store, Before& before, After& after) {
+  template <int NS, int R, int... Rest, class TW, class Mem, class Store, class Before, class After>
+  __device__ __forceinline__ static void run(float2 (&v)[E], int t, const TW& tw, Mem& mem, Store& store,
+                                             Before& before, After& after) {
     compute<R, NS>(v, t, tw);
     if constexpr (sizeof...(Rest) == 0) {
       static_assert(NS * R == N, "radix list does not multiply to N");
@@ -292,20 +369,19 @@ struct Stockham {
     }
   }
 
-  template <int... Rs, class Mem, class Store, class Before, class After>
-  __device__ __forceinline__ static void run_all(Radices<Rs...>, float2 (&v)[E], int t,
-                                                 const float2* __restrict__ tw, Mem& mem, Store& store,
-                                                 Before& before, After& after) {
+  template <int... Rs, class TW, class Mem, class Store, class Before, class After>
+  __device__ __forceinline__ static void run_all(Radices<Rs...>, float2 (&v)[E], int t, const TW& tw, Mem& mem,
+                                                 Store& store, Before& before, After& after) {
     run<1, Rs...>(v, t, tw, mem, store, before, after);
   }
 };
 
 // Convenience wrapper: load the first-stage inputs with load(n) and run the whole transform,
 // with before() / after() around the first block barrier (see Stockham::run).
-template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store, class Before,
-          class After>
-__device__ __forceinline__ void fft_1d_hooked(int t, const float2* __restrict__ tw, Load& load, Mem& mem,
-                                              Store& store, Before& before, After& after) {
+template <int N, int TWS, bool INV, class C = FFTConf<N>, class TW, class Load, class Mem, class Store,
+          class Before, class After>
+__device__ __forceinline__ void fft_1d_hooked(int t, const TW& tw, Load& load, Mem& mem, Store& store,
+                                              Before& before, After& after) {
   static_assert(C::N == N, "configuration of another length");
   constexpr int E = C::E, T = C::T;
   constexpr int R0 = FirstRadix<typename C::radices>::value;
@@ -317,8 +393,8 @@ __device__ __forceinline__ void fft_1d_hooked(int t, const float2* __restrict__ 
   Stockham<N, E, TWS, INV>::run_all(typename C::radices{}, v, t, tw, mem, store, before, after);
 }
 
-template <int N, int TWS, bool INV, class C = FFTConf<N>, class Load, class Mem, class Store>
-__device__ __forceinline__ void fft_1d(int t, const float2* __restrict__ tw, Load& load, Mem& mem, Store& store) {
+template <int N, int TWS, bool INV, class C = FFTConf<N>, class TW, class Load, class Mem, class Store>
+__device__ __forceinline__ void fft_1d(int t, const TW& tw, Load& load, Mem& mem, Store& store) {
   auto none = [] {};
   fft_1d_hooked<N, TWS, INV, C>(t, tw, load, mem, store, none, none);
 }

@@ -18,6 +18,25 @@ __device__ __forceinline__ int tile_key(const Tiles& tl, int cy, int cz) {
   return tile_bin(tl, ty, tz) * 4 + ry + rz;
 }
 
+// Tile key of particle p with displacement (sx, sy, sz); flags a non-finite displacement.
+__device__ __forceinline__ int particle_key(const Geometry& g, const Tiles& tl, int64_t p, float sx, float sy,
+                                            float sz, int* __restrict__ err) {
+  int ix, iy, iz;
+  lattice_index(g, p, ix, iy, iz);
+  if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) atomicOr(err, kErrNonFinite);
+  int cy, ty, cz, tz;
+  fixed_axis(g, iy, sy, cy, ty);
+  fixed_axis(g, iz, sz, cz, tz);
+  return tile_key(tl, cy, cz);
+}
+
+// counts[key] += 1 for the key of every live lane, one atomic per distinct key in the warp
+__device__ __forceinline__ void count_key(int key, bool live, int* __restrict__ counts) {
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+}
+
 // Bin key of particle p (plus bin_base) into keys[p]; counts[key] += 1 with one atomic per
 // distinct key in the warp.  s is the box's SoA [3][np^3] displacement.
 __device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s, int64_t p,
@@ -25,19 +44,39 @@ __device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, co
                                           int* __restrict__ err) {
   int key = -1;
   if (live) {
-    int ix, iy, iz;
-    lattice_index(g, p, ix, iy, iz);
-    const float sy = s[g.np3 + p], sz = s[2 * g.np3 + p];
-    if (!isfinite(s[p]) || !isfinite(sy) || !isfinite(sz)) atomicOr(err, kErrNonFinite);
-    int cy, ty, cz, tz;
-    fixed_axis(g, iy, sy, cy, ty);
-    fixed_axis(g, iz, sz, cz, tz);
-    key = bin_base + tile_key(tl, cy, cz);
+    key = bin_base + particle_key(g, tl, p, s[p], s[g.np3 + p], s[2 * g.np3 + p], err);
     keys[p] = key;
   }
+  count_key(key, live, counts);
+}
+
+// Record of particle p: fixed-point CIC coordinates and lattice index (see scatter_body).
+__device__ __forceinline__ uint4 particle_record(const Geometry& g, int64_t p, float sx, float sy, float sz) {
+  int ix, iy, iz;
+  lattice_index(g, p, ix, iy, iz);
+  const int li[3] = {ix, iy, iz};
+  const float sd[3] = {sx, sy, sz};
+  uint32_t f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int c, t;
+    fixed_axis(g, li[d], sd[d], c, t);
+    f[d] = ((uint32_t)c << g.fbits) | (uint32_t)t;
+  }
+  return make_uint4(f[0], f[1], f[2], (uint32_t)p);
+}
+
+// rec[cursor[key]++] = r for every live lane (one atomic per distinct key in the warp; lanes
+// with the same key take consecutive slots in lane order)
+__device__ __forceinline__ void place_record(int key, bool live, uint4 r, int* __restrict__ cursor,
+                                             uint4* __restrict__ rec) {
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
-  if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (live) rec[base + __popc(peers & ((1u << lane) - 1u))] = r;
 }
 
 // Counting-sort scatter: pos = cursor[keys[p]]++ (one atomic per distinct key in the warp) and
@@ -48,26 +87,8 @@ __device__ __forceinline__ void scatter_body(const Geometry& g, const float* __r
                                              const int* __restrict__ keys, int* __restrict__ cursor,
                                              uint4* __restrict__ rec) {
   const int key = live ? keys[p] : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  const int rank = __popc(peers & ((1u << lane) - 1u));
-  if (live) {
-    int ix, iy, iz;
-    lattice_index(g, p, ix, iy, iz);
-    const int li[3] = {ix, iy, iz};
-    uint32_t f[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      int c, t;
-      fixed_axis(g, li[d], s[d * g.np3 + p], c, t);
-      f[d] = ((uint32_t)c << g.fbits) | (uint32_t)t;
-    }
-    rec[base + rank] = make_uint4(f[0], f[1], f[2], (uint32_t)p);
-  }
+  const uint4 r = live ? particle_record(g, p, s[p], s[g.np3 + p], s[2 * g.np3 + p]) : make_uint4(0, 0, 0, 0);
+  place_record(key, live, r, cursor, rec);
 }
 
 // CIC gather of the three force meshes fmesh [3][ng^3] for a cloud that starts at cells c with

@@ -38,9 +38,10 @@ __host__ __device__ constexpr int half_pitch() {
 
 // block (bx, slab): W columns of one slab of the in-place strided FFT (T(N) * W threads);
 // smem: N W float2.  Element (n, col) at data[slab * slab_stride + n * row_stride + col].
-template <int N, int W, bool INV, class C = FFTConf<N>>
+// (tw: the base twiddle table or an SmemTw stage table)
+template <int N, int W, bool INV, class C = FFTConf<N>, class TW>
 __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride,
-                                          int ncols, const float2* __restrict__ tw, int bx, int slab, float2* smem) {
+                                          int ncols, const TW& tw, int bx, int slab, float2* smem) {
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int col = bx * W + w;
   const bool valid = col < ncols;
@@ -309,6 +310,12 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
 // the forward transform's last stage, then the inverse transforms of i k_z phi (-> Gz) and of phi
 // (-> A, in place).  block (bx, ky): W columns kx of the slab ky (T(N) * W threads);
 // sm: N W float2 + (N + W) floats (sinc^2 tables).
+// shared-memory layout of the wide z pass: strip (N W float2), sinc^2 tables (N + W floats,
+// rounded up to 16 bytes), stage twiddle table
+template <int N, int W>
+__host__ __device__ constexpr int wide_z_table_offset() {
+  return N * W + (N + W + 3) / 4 * 2;
+}
 template <int N, int W, class C = FFTConf<N>>
 __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz, float kf,
                                                   int deconv, float norm, const float2* __restrict__ tw, int bx,
@@ -317,6 +324,9 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
   float2* S = sm;
   float* sz2 = reinterpret_cast<float*>(sm + N * W);
   float* sx2 = sz2 + N;
+  float2* stab = sm + wide_z_table_offset<N, W>();
+  stw_fill<C, 1>(stab, tw, threadIdx.x, NT);
+  const SmemTw<C> stw{stab};
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = bx * W + w;
   const bool valid = kx < nh;
@@ -349,7 +359,7 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
       }
       if (valid) a[n * zstride] = c_scale(x, gk);
     };
-    fft_1d<N, 1, false, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, false, C>(t, stw, load, mem, store);
   }
   __syncthreads();  // phi of the strip is in A (global writes of this block, visible after the barrier)
   {
@@ -360,14 +370,14 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
     auto store = [&](int n, float2 x) {
       if (valid) gz[n * zstride] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 { return valid ? __ldcg(a + n * zstride) : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) a[n * zstride] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
 }
 
@@ -379,6 +389,9 @@ __device__ __forceinline__ void y_inv3_wide_body(float2* __restrict__ B, float2*
                                                  float2* __restrict__ Gz, float kf, const float2* __restrict__ tw,
                                                  int bx, int z, float2* sm) {
   constexpr int nh = N / 2 + 1, T = C::T, P = half_pitch<N>();
+  float2* stab = sm + N * W;
+  stw_fill<C, 1>(stab, tw, threadIdx.x, T * W);
+  const SmemTw<C> stw{stab};
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = bx * W + w;
   const bool valid = kx < nh;
@@ -398,21 +411,21 @@ __device__ __forceinline__ void y_inv3_wide_body(float2* __restrict__ B, float2*
     auto store = [&](int n, float2 x) {
       if (valid) gy[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 { return valid ? b[(int64_t)n * P] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) b[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 { return valid ? gz[(int64_t)n * P] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) gz[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
 }
 

@@ -7,10 +7,15 @@ namespace cola {
 // Lattice index of particle p = (iz np + iy) np + ix.
 __device__ __forceinline__ void lattice_index(const Geometry& g, int64_t p, int& ix, int& iy, int& iz) {
   if (g.np3 <= 0xFFFFFFFFLL) {
+    // quotients by np as multiply-highs (set_np_divider): integer-pipe instructions only
     const unsigned pu = (unsigned)p, n = (unsigned)g.np;
-    const unsigned r = pu / n;
+    auto div_np = [&](unsigned v) -> unsigned {
+      const unsigned t = __umulhi(g.np_mul, v);
+      return (t + ((v - t) >> g.np_sh1)) >> g.np_sh2;
+    };
+    const unsigned r = div_np(pu);
     ix = (int)(pu - r * n);
-    iz = (int)(r / n);
+    iz = (int)div_np(r);
     iy = (int)(r - (unsigned)iz * n);
   } else {
     const int64_t r = p / g.np;
@@ -30,7 +35,14 @@ __device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, in
   const int64_t q = g.ratio ? ((int64_t)i * g.ratio) << g.fbits : (((int64_t)i * g.ng) << g.fbits) / g.np;
   const float w = __fmul_rn(s, g.scale32);
   const float ws = __fmul_rn(w, (float)one);  // exact: power-of-two scaling
-  int64_t f = q + (int64_t)floorf(ws);
+  int64_t f;
+  if (fabsf(ws) < 4194304.0f) {
+    // floor(ws) for |ws| < 2^22 without a conversion instruction: ws + 1.5 2^23 rounded down
+    // lies in [2^23, 2^24), where floats are the integers and their bit patterns consecutive
+    f = q + (int64_t)(__float_as_int(__fadd_rd(ws, 12582912.0f)) - 0x4B400000);
+  } else {
+    f = q + (int64_t)floorf(ws);
+  }
   if (f < 0) f += period;
   if (f >= period) f -= period;
   if (f < 0 || f >= period) {  // displacement beyond one box length

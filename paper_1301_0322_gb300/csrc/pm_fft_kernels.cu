@@ -64,7 +64,7 @@ template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
     k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float kf, int deconv, float norm,
                        const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   z_green_wide_body<N, W>(A, Gz, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
 }
 
@@ -72,7 +72,7 @@ template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
     k_fft_y_inv3_wide(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz, float kf,
                       const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   y_inv3_wide_body<N, W>(B, Gy, Gz, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
@@ -80,9 +80,12 @@ __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
 template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
     k_fft_y_fwd_wide(float2* __restrict__ A, const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   constexpr int P = half_pitch<N>();
-  cols_body<N, W, false>(A, (int64_t)N * P, P, N / 2 + 1, tw, blockIdx.x, blockIdx.y, sm);
+  float2* stab = sm + N * W;
+  stw_fill<FFTConf<N>, 1>(stab, tw, threadIdx.x, FFTConf<N>::T * W);
+  const SmemTw<FFTConf<N>> stw{stab};
+  cols_body<N, W, false>(A, (int64_t)N * P, P, N / 2 + 1, stw, blockIdx.x, blockIdx.y, sm);
 }
 
 // Persistent: each block walks items blockIdx.x, blockIdx.x + gridDim.x, ... with the bulk
@@ -199,7 +202,7 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     constexpr int NT = FFTConf<N>::T * WW;
     // 2. forward y pass
     {
-      const size_t smem = sizeof(float2) * N * WW;
+      const size_t smem = sizeof(float2) * (N * WW + stw_size<FFTConf<N>>());
       if ((rc = set_smem(k_fft_y_fwd_wide<N, WW>, smem))) return rc;
       LaunchScope ls_(flabel<N>(4), st);
       k_fft_y_fwd_wide<N, WW><<<grid, NT, smem, st>>>(A, tw);
@@ -207,7 +210,7 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     }
     // 3. z pass with the Green's function
     {
-      const size_t smem = sizeof(float2) * N * WW + sizeof(float) * (N + WW);
+      const size_t smem = sizeof(float2) * (wide_z_table_offset<N, WW>() + stw_size<FFTConf<N>>());
       if ((rc = set_smem(k_fft_z_green_wide<N, WW>, smem))) return rc;
       LaunchScope ls_(flabel<N>(1), st);
       k_fft_z_green_wide<N, WW><<<grid, NT, smem, st>>>(A, Gz, kf, deconv, norm, tw);
@@ -215,7 +218,7 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     }
     // 4. inverse y passes
     {
-      const size_t smem = sizeof(float2) * N * WW;
+      const size_t smem = sizeof(float2) * (N * WW + stw_size<FFTConf<N>>());
       if ((rc = set_smem(k_fft_y_inv3_wide<N, WW>, smem))) return rc;
       LaunchScope ls_(flabel<N>(2), st);
       k_fft_y_inv3_wide<N, WW><<<grid, NT, smem, st>>>(A, Gy, Gz, kf, tw);

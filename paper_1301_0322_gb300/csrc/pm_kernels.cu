@@ -13,10 +13,37 @@
 namespace cola {
 
 // ---- binning -------------------------------------------------------------------------------
-__global__ void k_keys(Geometry g, Tiles tl, const float* __restrict__ s, int* __restrict__ keys,
-                       int* __restrict__ counts, int* __restrict__ err) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  keys_body(g, tl, s, p, p < g.np3, 0, keys, counts, err);
+// Four particles per thread: a warp takes 128 consecutive particles, lane l the particles
+// 32 u + l (u = 0..3), whose loads are all in flight together: four times the bytes in flight
+// per thread of k_keys (bound by memory latency at one particle per thread), while every round
+// u still covers 32 consecutive particles (as few distinct keys per warp as k_keys).
+constexpr int kPartPerThread = 4;
+__global__ void __launch_bounds__(256) k_keys_x4(Geometry g, Tiles tl, const float* __restrict__ s,
+                                                 int* __restrict__ keys, int* __restrict__ counts,
+                                                 int* __restrict__ err) {
+  constexpr int U = kPartPerThread;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U + (threadIdx.x & 31);
+  float sx[U], sy[U], sz[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    if (p < g.np3) {
+      sx[u] = __ldg(s + p);
+      sy[u] = __ldg(s + g.np3 + p);
+      sz[u] = __ldg(s + 2 * g.np3 + p);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    const bool live = p < g.np3;
+    int key = -1;
+    if (live) {
+      key = particle_key(g, tl, p, sx[u], sy[u], sz[u], err);
+      keys[p] = key;
+    }
+    count_key(key, live, counts);
+  }
 }
 
 // Exclusive scan of the bin counts in three launches (block sums, scan of the block sums,
@@ -83,10 +110,32 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ co
   if (i == n - 1) offsets[n] = excl + x;
 }
 
-__global__ void k_scatter(Geometry g, const float* __restrict__ s, const int* __restrict__ keys,
-                          int* __restrict__ cursor, uint4* __restrict__ rec) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  scatter_body(g, s, p, p < g.np3, keys, cursor, rec);
+// four particles per thread, as k_keys_x4 (round u places 32 consecutive particles: a bin's
+// records stay in lattice order within each warp)
+__global__ void __launch_bounds__(256) k_scatter_x4(Geometry g, const float* __restrict__ s,
+                                                    const int* __restrict__ keys, int* __restrict__ cursor,
+                                                    uint4* __restrict__ rec) {
+  constexpr int U = kPartPerThread;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U + (threadIdx.x & 31);
+  int k[U];
+  float sx[U], sy[U], sz[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    k[u] = -1;
+    if (p < g.np3) {
+      k[u] = __ldg(keys + p);
+      sx[u] = __ldg(s + p);
+      sy[u] = __ldg(s + g.np3 + p);
+      sz[u] = __ldg(s + 2 * g.np3 + p);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    const bool live = p < g.np3;
+    place_record(k[u], live, live ? particle_record(g, p, sx[u], sy[u], sz[u]) : uint4{}, cursor, rec);
+  }
 }
 
 // ---- deposit ----------------------------------------------------------------------------------
@@ -301,7 +350,7 @@ static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 int launch_keys(const Geometry& g, const Tiles& t, const float* s, int* keys, int* counts, int* err, cudaStream_t st) {
   { LaunchScope ls_("keys", st);
-  k_keys<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, t, s, keys, counts, err); }
+  k_keys_x4<<<blocks_for(g.np3, 256 * kPartPerThread), 256, 0, st>>>(g, t, s, keys, counts, err); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
@@ -331,7 +380,7 @@ int launch_scan(const Tiles& t, int* counts, int* offsets, int* cursor, int* blo
 int launch_scatter(const Geometry& g, const float* s, const int* keys, int* cursor, uint4* rec,
                    cudaStream_t st) {
   { LaunchScope ls_("scatter", st);
-  k_scatter<<<blocks_for(g.np3, 256), 256, 0, st>>>(g, s, keys, cursor, rec); }
+  k_scatter_x4<<<blocks_for(g.np3, 256 * kPartPerThread), 256, 0, st>>>(g, s, keys, cursor, rec); }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
