@@ -103,7 +103,7 @@ __device__ __noinline__ void deposit_tile(const BoxDesc* __restrict__ d, const u
                                           const int* __restrict__ offsets, int tile) {
   extern __shared__ __align__(16) unsigned long long ens_smem[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ, CM>(d->g, d->tl, rec, offsets, d->A, d->P, d->tw, d->dscale, d->err, tile, ens_smem,
+  deposit_fftx_body<N, TY, TZ, CM>(d->g, d->tl, rec, offsets, d->A, d->P, d->tw, d->tw, d->dscale, d->err, tile, ens_smem,
                                    ints);
 }
 

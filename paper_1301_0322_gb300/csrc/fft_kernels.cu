@@ -27,13 +27,28 @@ __host__ __device__ constexpr int cols_pass_min_blocks() {
   return FFTConf<N>::T * cols_pass_width<N>() >= 1024 ? 1 : 2;
 }
 
+// Stage twiddles from a shared-memory table (fft.cuh) at N = 2048, where one block per SM leaves
+// room for it; at the other lengths the table would cost resident blocks.
+template <int N>
+__host__ __device__ constexpr int cols_table_size() {
+  return N == 2048 ? stw_size<FFTConf<N>>() : 0;
+}
+
 // In-place FFT of ncols columns per slab: element (n, col) at data[slab*slab_stride + n*row_stride + col].
 template <int N, bool INV>
 __global__ void __launch_bounds__(FFTConf<N>::T * cols_pass_width<N>(), cols_pass_min_blocks<N>())
     k_fft_cols(float2* __restrict__ data, int64_t slab_stride, int64_t row_stride, int ncols,
                const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  cols_body<N, cols_pass_width<N>(), INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
+  extern __shared__ __align__(16) float2 smem[];
+  constexpr int W = cols_pass_width<N>();
+  if constexpr (cols_table_size<N>() > 0) {
+    float2* stab = smem + N * W;
+    stw_fill<FFTConf<N>, 1>(stab, tw, threadIdx.x, FFTConf<N>::T * W);
+    cols_body<N, W, INV>(data, slab_stride, row_stride, ncols, SmemTw<FFTConf<N>>{stab}, blockIdx.x, blockIdx.y,
+                         smem);
+  } else {
+    cols_body<N, W, INV>(data, slab_stride, row_stride, ncols, tw, blockIdx.x, blockIdx.y, smem);
+  }
 }
 
 // Real rows of length N -> half-spectrum rows (N/2 + 1 entries, stride P), via a complex
@@ -137,7 +152,7 @@ template <int N>
 static int cols(bool inverse, float2* data, int64_t nslabs, int64_t slab_stride, int64_t row_stride, int ncols,
                 const float2* tw, cudaStream_t st) {
   constexpr int W = cols_pass_width<N>();
-  const size_t smem = (size_t)N * W * sizeof(float2);
+  const size_t smem = (size_t)(N * W + cols_table_size<N>()) * sizeof(float2);
   if (nslabs > 65535) return fail(COLA_EINVAL, "fft column pass: too many slabs");
   dim3 grid((ncols + W - 1) / W, (unsigned)nslabs);
   if (inverse) {

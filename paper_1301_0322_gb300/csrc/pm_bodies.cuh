@@ -59,11 +59,13 @@ __device__ __forceinline__ void cols_body(float2* __restrict__ data, int64_t sla
 // bytes of shared memory (the cells' low 32-bit words, then their high words; afterwards the
 // rows' transform buffers); ints: 28 ints of shared memory
 // rec: the bin-ordered particle records (fixed-point CIC coordinates; offsets index them directly)
-template <int N, int TY, int TZ, class CM = FFTConf<N / 2>>
+// (stw: the row transform's stage twiddles, the base table tw or an SmemTw table)
+template <int N, int TY, int TZ, class CM = FFTConf<N / 2>, class STW>
 __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles& tl, const uint4* __restrict__ rec,
                                                   const int* __restrict__ offsets, float2* __restrict__ out, int P,
-                                                  const float2* __restrict__ tw, float dscale, int* __restrict__ err,
-                                                  int tile, unsigned long long* acc, int* ints) {
+                                                  const float2* __restrict__ tw, const STW& stw, float dscale,
+                                                  int* __restrict__ err, int tile, unsigned long long* acc,
+                                                  int* ints) {
   constexpr int M = N / 2, T = CM::T, ROWS = TY * TZ, LD = xrow_ld<M>(), NT = T * ROWS, R0 = first_radix<CM>();
   int* rbeg = ints;
   int* rpre = ints + 9;
@@ -161,7 +163,7 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
   };
   auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   auto store = [&](int n, float2 x) { buf[xpad<R0>(n)] = x; };
-  fft_1d<M, 2, false, CM>(t, tw, load, mem, store);
+  fft_1d<M, 2, false, CM>(t, stw, load, mem, store);
   if (overflow) atomicOr(err, kErrOverflow);
   __syncthreads();
   const int lz = w / TY, ly = w - lz * TY;
@@ -182,10 +184,10 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
 
 // ---- 3. z pass with the Green's function ------------------------------------------------------------
 // block (bx, ky): W columns kx of the slab ky (T(N) * W threads); sm: 2 N W float2
-template <int N, int W, class C = FFTConf<N>>
+// (stw: the stage twiddles, the base table tw or an SmemTw table)
+template <int N, int W, class C = FFTConf<N>, class STW>
 __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __restrict__ Gz, int P, float kf,
-                                             int deconv, float norm, const float2* __restrict__ tw, int bx, int ky,
-                                             float2* sm) {
+                                             int deconv, float norm, const STW& stw, int bx, int ky, float2* sm) {
   constexpr int nh = N / 2 + 1, NT = C::T * W;
   float2* S0 = sm;           // delta_k of the slab, [n][W]
   float2* S1 = sm + N * W;   // exchange buffer
@@ -199,7 +201,7 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
   {
     auto load = [&](int n) -> float2 { return valid ? a[n * zstride] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) { S0[n * W + w] = x; };
-    fft_1d<N, 1, false, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, false, C>(t, stw, load, mem, store);
   }
   // sinc^2 tables of the z index and of the block's W columns, then
   // phi_k = delta_k norm / (k^2 W(k)^p) in place in S0 with one division per mode
@@ -238,7 +240,7 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
     auto store = [&](int n, float2 x) {
       if (valid) a[n * zstride] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 {
@@ -248,16 +250,15 @@ __device__ __forceinline__ void z_green_body(float2* __restrict__ A, float2* __r
     auto store = [&](int n, float2 x) {
       if (valid) gz[n * zstride] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
 }
 
 // ---- 4. inverse y passes ------------------------------------------------------------------------------------
 // block (bx, z): W columns kx of the slab z (T(N) * W threads); sm: 2 N W float2
-template <int N, int W, class C = FFTConf<N>>
+template <int N, int W, class C = FFTConf<N>, class STW>
 __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __restrict__ Gy, float2* __restrict__ Gz,
-                                            int P, float kf, const float2* __restrict__ tw, int bx, int z,
-                                            float2* sm) {
+                                            int P, float kf, const STW& stw, int bx, int z, float2* sm) {
   constexpr int nh = N / 2 + 1, T = C::T;
   float2* S0 = sm;
   float2* S1 = sm + N * W;
@@ -279,7 +280,7 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
     auto store = [&](int n, float2 x) {
       if (valid) b[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 {
@@ -289,14 +290,14 @@ __device__ __forceinline__ void y_inv3_body(float2* __restrict__ B, float2* __re
     auto store = [&](int n, float2 x) {
       if (valid) gy[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
     auto load = [&](int n) -> float2 { return valid ? gz[(int64_t)n * P] : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) gz[(int64_t)n * P] = x;
     };
-    fft_1d<N, 1, true, C>(t, tw, load, mem, store);
+    fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
 }
 
@@ -451,9 +452,10 @@ __device__ __forceinline__ void c2r3_issue(float2* stage, const float2* src_rows
 }
 
 // Inverse x transform of the staged rows into F rows (pitch N floats); comp 0 applies i k_x.
-template <int N, int RB, class CM = FFTConf<N / 2>>
+// tw: the base twiddle table; stw: the stage twiddles (the base table or an SmemTw table)
+template <int N, int RB, class CM = FFTConf<N / 2>, class STW>
 __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ Frows, int comp, float kf,
-                                             const float2* __restrict__ tw) {
+                                             const float2* __restrict__ tw, const STW& stw) {
   constexpr int M = N / 2, T = CM::T, LD = xrow_ld<M>(), R0 = first_radix<CM>();
   static_assert(T * RB <= 1024, "block too large");
   const int t = threadIdx.x % T, w = threadIdx.x / T;
@@ -471,7 +473,12 @@ __device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ 
   auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   float2* dst = reinterpret_cast<float2*>(Frows + (int64_t)w * N);
   auto store = [&](int n, float2 x) { dst[n] = x; };
-  fft_1d<M, 2, true, CM>(t, tw, load, mem, store);
+  fft_1d<M, 2, true, CM>(t, stw, load, mem, store);
+}
+template <int N, int RB, class CM = FFTConf<N / 2>>
+__device__ __forceinline__ void c2r3_compute(float2* stage, float* __restrict__ Frows, int comp, float kf,
+                                             const float2* __restrict__ tw) {
+  c2r3_compute<N, RB, CM>(stage, Frows, comp, kf, tw, tw);
 }
 
 }  // namespace cola

@@ -23,14 +23,21 @@ __host__ __device__ constexpr int deposit_min_blocks() {
   return N == 2048 && TY * TZ == 4 ? 3 : ((512 / (FFTConf<N / 2>::T * TY * TZ)) > 0 ? 512 / (FFTConf<N / 2>::T * TY * TZ) : 1);
 }
 
+// cell sums (8 bytes per cell) of a TY x TZ tile, which later hold the rows' transform buffers
+template <int N, int TY, int TZ>
+__host__ __device__ constexpr int deposit_acc_cells() {
+  return TY * TZ * (N > xrow_ld<N / 2>() ? N : xrow_ld<N / 2>());
+}
+
 template <int N, int TY, int TZ>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, deposit_min_blocks<N, TY, TZ>())
     k_deposit_fftx(Geometry g, Tiles tl, const uint4* __restrict__ rec, const int* __restrict__ offsets,
                    float2* __restrict__ out, int P, const float2* __restrict__ tw, float dscale,
                    int* __restrict__ err) {
+  // (a shared-memory stage twiddle table costs more in resident blocks than it saves here)
   extern __shared__ unsigned long long acc[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, dscale, err, blockIdx.x, acc, ints);
+  deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, tw, dscale, err, blockIdx.x, acc, ints);
 }
 
 template <int N>
@@ -115,6 +122,10 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), c2r3_min_b
     const float2* m = comp == 0 ? C : (comp == 1 ? Gy : Gz);
     return m + (item - comp * nrb) * RB * P;
   };
+  // stage twiddles, copied once per block (persistent) behind the staging buffers
+  float2* stab = c2r_stage + NB * RB * LD;
+  stw_fill<FFTConf<M>, 2>(stab, tw, threadIdx.x, blockDim.x);
+  const SmemTw<FFTConf<M>> stw{stab};
   if (threadIdx.x == 0) {
     for (int k = 0; k < NB; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * c2r3_rows<N>(), c2r3_min_b
     }
     const int comp = (int)(item / nrb);
     const int64_t row0 = (item - comp * nrb) * RB;
-    c2r3_compute<N, RB>(c2r_stage + b * RB * LD, F + (int64_t)comp * N * N * N + row0 * N, comp, kf, tw);
+    c2r3_compute<N, RB>(c2r_stage + b * RB * LD, F + (int64_t)comp * N * N * N + row0 * N, comp, kf, tw, stw);
     __syncthreads();
   }
 }
@@ -179,13 +190,13 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     const double n3 = (double)N * N * N;
     const float dscale = (float)(n3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
     if (tl.ty == 4 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * 8 * std::max(N, xrow_ld<M>());
+      const size_t smem = sizeof(unsigned long long) * deposit_acc_cells<N, 4, 2>();
       if ((rc = set_smem(k_deposit_fftx<N, 4, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
       k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, rec, offsets, A, P, tw,
                                                                                   dscale, err);
     } else if (tl.ty == 2 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * 4 * std::max(N, xrow_ld<M>());
+      const size_t smem = sizeof(unsigned long long) * deposit_acc_cells<N, 2, 2>();
       if ((rc = set_smem(k_deposit_fftx<N, 2, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
       k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, rec, offsets, A, P, tw,
@@ -249,7 +260,7 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
   // 5. inverse x passes (persistent, bulk-copy pipelined)
   {
     constexpr int RB = c2r3_rows<N>(), T = FFTConf<M>::T;
-    const size_t smem = sizeof(float2) * c2r3_stages<N>() * RB * xrow_ld<M>();
+    const size_t smem = sizeof(float2) * (c2r3_stages<N>() * RB * xrow_ld<M>() + stw_size<FFTConf<M>>());
     if ((rc = set_smem(k_fft_x_c2r3<N>, smem))) return rc;
     const int64_t nrows = (int64_t)N * N;
     if (nrows % RB) return fail(COLA_EINVAL, "fused c2r: row count not a multiple of the block rows");
