@@ -214,30 +214,32 @@ __host__ __device__ constexpr int xrow_ld() {
 // 8-byte loads per butterfly; a block may instead copy every stage's twiddles once into shared
 // memory, butterfly by butterfly, and read them as 16-byte pairs.  Row pitch stw_pitch(R) float2
 // (an even count, 2 mod 4): eight consecutive butterflies' pair loads fall on distinct banks.
-__host__ __device__ constexpr int stw_pitch(int R) {
+// A tight table (TIGHT) gives radix-4 stages pitch 4 instead of 6: two-way bank conflicts on
+// the pair loads, a third less shared memory for the largest stage of a 1024-point transform.
+__host__ __device__ constexpr int stw_pitch(int R, bool tight = false) {
   const int pairs = R / 2;  // ceil((R - 1) / 2)
-  return 2 * pairs + ((pairs % 2 == 0) ? 2 : 0);
+  return (tight && R == 4) ? 4 : 2 * pairs + ((pairs % 2 == 0) ? 2 : 0);
 }
 template <int... Rs>
-__host__ __device__ constexpr int stw_offset_of(Radices<Rs...>, int ns_target) {
+__host__ __device__ constexpr int stw_offset_of(Radices<Rs...>, int ns_target, bool tight = false) {
   int ns = 1, off = 0;
   for (int r : {Rs...}) {
     if (ns == ns_target) return off;
-    if (ns > 1) off += ns * stw_pitch(r);
+    if (ns > 1) off += ns * stw_pitch(r, tight);
     ns *= r;
   }
   return off;
 }
 // float2 entries of the table of configuration C
-template <class C>
+template <class C, bool TIGHT = false>
 __host__ __device__ constexpr int stw_size() {
-  return stw_offset_of(typename C::radices{}, C::N);
+  return stw_offset_of(typename C::radices{}, C::N, TIGHT);
 }
 
 // Fill the table of configuration C from the base table tw (stage twiddle m at tw[m * TWS]):
 // threads tid = 0 .. nth - 1 of the block; the first use comes after the transform's first
 // block barrier, so the fill needs no barrier of its own.
-template <int N, int TWS, int... Rs>
+template <int N, int TWS, bool TIGHT, int... Rs>
 __device__ __forceinline__ void stw_fill_stages(Radices<Rs...>, float2* dst, const float2* __restrict__ tw,
                                                 int tid, int nth) {
   int ns = 1, off = 0;
@@ -245,7 +247,7 @@ __device__ __forceinline__ void stw_fill_stages(Radices<Rs...>, float2* dst, con
       [&] {
         constexpr int R = Rs;
         if (ns > 1) {
-          const int p = stw_pitch(R), cnt = ns * (R - 1), step = N / (ns * R);
+          const int p = stw_pitch(R, TIGHT), cnt = ns * (R - 1), step = N / (ns * R);
           for (int i = tid; i < cnt; i += nth) {
             const int j = i / (R - 1), r = i - j * (R - 1) + 1;
             dst[off + j * p + r - 1] = __ldg(tw + (int64_t)j * r * step * TWS);
@@ -256,18 +258,18 @@ __device__ __forceinline__ void stw_fill_stages(Radices<Rs...>, float2* dst, con
       }(),
       ...);
 }
-template <class C, int TWS>
+template <class C, int TWS, bool TIGHT = false>
 __device__ __forceinline__ void stw_fill(float2* dst, const float2* __restrict__ tw, int tid, int nth) {
-  stw_fill_stages<C::N, TWS>(typename C::radices{}, dst, tw, tid, nth);
+  stw_fill_stages<C::N, TWS, TIGHT>(typename C::radices{}, dst, tw, tid, nth);
 }
 
 // twiddle source reading the shared-memory table of configuration C (16-byte aligned)
-template <class C>
+template <class C, bool TIGHT = false>
 struct SmemTw {
   const float2* base;
   template <int R, int NS, bool INV>
   __device__ __forceinline__ void apply(unsigned j, float2* x) const {
-    constexpr int off = stw_offset_of(typename C::radices{}, NS), p = stw_pitch(R);
+    constexpr int off = stw_offset_of(typename C::radices{}, NS, TIGHT), p = stw_pitch(R, TIGHT);
     const float4* q = reinterpret_cast<const float4*>(base + off + j * p);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {

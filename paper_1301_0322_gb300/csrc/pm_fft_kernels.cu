@@ -28,16 +28,29 @@ template <int N, int TY, int TZ>
 __host__ __device__ constexpr int deposit_acc_cells() {
   return TY * TZ * (N > xrow_ld<N / 2>() ? N : xrow_ld<N / 2>());
 }
+// A tight stage twiddle table (fft.cuh) behind the cell sums at N = 2048 (10.3 KB: three blocks
+// of 2 x 2 tiles per SM still fit); below 2048 the table costs more in resident blocks than the
+// twiddle loads it saves.
+template <int N>
+__host__ __device__ constexpr int deposit_table_size() {
+  return N == 2048 ? stw_size<FFTConf<N / 2>, true>() : 0;
+}
 
 template <int N, int TY, int TZ>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * TY * TZ, deposit_min_blocks<N, TY, TZ>())
     k_deposit_fftx(Geometry g, Tiles tl, const uint4* __restrict__ rec, const int* __restrict__ offsets,
                    float2* __restrict__ out, int P, const float2* __restrict__ tw, float dscale,
                    int* __restrict__ err) {
-  // (a shared-memory stage twiddle table costs more in resident blocks than it saves here)
-  extern __shared__ unsigned long long acc[];
+  extern __shared__ __align__(16) unsigned long long acc[];
   __shared__ int ints[28];
-  deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, tw, dscale, err, blockIdx.x, acc, ints);
+  if constexpr (deposit_table_size<N>() > 0) {
+    float2* stab = reinterpret_cast<float2*>(acc + deposit_acc_cells<N, TY, TZ>());
+    stw_fill<FFTConf<N / 2>, 2, true>(stab, tw, threadIdx.x, blockDim.x);
+    deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, SmemTw<FFTConf<N / 2>, true>{stab}, dscale, err,
+                                 blockIdx.x, acc, ints);
+  } else {
+    deposit_fftx_body<N, TY, TZ>(g, tl, rec, offsets, out, P, tw, tw, dscale, err, blockIdx.x, acc, ints);
+  }
 }
 
 template <int N>
@@ -190,13 +203,13 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     const double n3 = (double)N * N * N;
     const float dscale = (float)(n3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
     if (tl.ty == 4 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * deposit_acc_cells<N, 4, 2>();
+      const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 4, 2>() + deposit_table_size<N>());
       if ((rc = set_smem(k_deposit_fftx<N, 4, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
       k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, rec, offsets, A, P, tw,
                                                                                   dscale, err);
     } else if (tl.ty == 2 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * deposit_acc_cells<N, 2, 2>();
+      const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 2, 2>() + deposit_table_size<N>());
       if ((rc = set_smem(k_deposit_fftx<N, 2, 2>, smem))) return rc;
       LaunchScope ls_(flabel<N>(0), st);
       k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, rec, offsets, A, P, tw,
