@@ -12,7 +12,7 @@
 namespace cola {
 
 // error bits latched in the workspace by kernels
-enum : int { kErrOverflow = 1, kErrNonFinite = 2, kErrTimeout = 4, kErrUnion = 8 };
+enum : int { kErrOverflow = 1, kErrNonFinite = 2, kErrTimeout = 4, kErrUnion = 8, kErrSmIds = 16 };
 
 // per-step float32 coefficients on the device (row of kCoef32 floats per force evaluation)
 enum Coef32 : int {

@@ -317,11 +317,29 @@ template <int N, int W>
 __host__ __device__ constexpr int wide_z_table_offset() {
   return N * W + (N + W + 3) / 4 * 2;
 }
+// scratch slots of the wide z pass (one per SM id, N W float2 each)
+constexpr int kZScratchSlots = 512;
+
+// z pass with the Green's function, one exchange buffer: the forward transform of the strip
+// (Green's function applied as it is stored) goes to a scratch slot of this SM, contiguous
+// [n][w]; the inverse transforms of i k_z phi (-> Gz) and of phi (-> A) read it back from L2
+// as whole 128-byte lines (the strip itself spans N rows 16.8 MB apart at N = 2048).  One block
+// fits per SM (shared memory), so the slot of %smid is this block's alone while it runs.
+// block (bx, ky): W columns kx of the slab ky (T(N) W threads); scratch: kZScratchSlots N W float2
 template <int N, int W, class C = FFTConf<N>>
-__device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz, float kf,
-                                                  int deconv, float norm, const float2* __restrict__ tw, int bx,
+__device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz,
+                                                  float2* __restrict__ scratch, float kf, int deconv, float norm,
+                                                  const float2* __restrict__ tw, int* __restrict__ err, int bx,
                                                   int ky, float2* sm) {
   constexpr int nh = N / 2 + 1, NT = C::T * W, P = half_pitch<N>();
+  unsigned smid, nsmid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+  if (nsmid > (unsigned)kZScratchSlots) {
+    if (threadIdx.x == 0) atomicOr(err, kErrSmIds);
+    return;
+  }
+  float2* sc = scratch + (int64_t)smid * (N * W);
   float2* S = sm;
   float* sz2 = reinterpret_cast<float*>(sm + N * W);
   float* sx2 = sz2 + N;
@@ -358,15 +376,15 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
         }
         gk = __fdividef(norm, den);
       }
-      if (valid) a[n * zstride] = c_scale(x, gk);
+      __stcg(sc + n * W + w, c_scale(x, gk));
     };
     fft_1d<N, 1, false, C>(t, stw, load, mem, store);
   }
-  __syncthreads();  // phi of the strip is in A (global writes of this block, visible after the barrier)
+  __syncthreads();  // phi of the strip is in the scratch slot (visible to the block after the barrier)
   {
     auto load = [&](int n) -> float2 {
       const float kz = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
-      return valid ? mul_ik(__ldcg(a + n * zstride), kz) : make_float2(0.f, 0.f);
+      return mul_ik(__ldcg(sc + n * W + w), kz);
     };
     auto store = [&](int n, float2 x) {
       if (valid) gz[n * zstride] = x;
@@ -374,7 +392,7 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
     fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
-    auto load = [&](int n) -> float2 { return valid ? __ldcg(a + n * zstride) : make_float2(0.f, 0.f); };
+    auto load = [&](int n) -> float2 { return __ldcg(sc + n * W + w); };
     auto store = [&](int n, float2 x) {
       if (valid) a[n * zstride] = x;
     };

@@ -82,11 +82,17 @@ __host__ __device__ constexpr int wide_min_blocks() {
 
 template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
-    k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float kf, int deconv, float norm,
-                       const float2* __restrict__ tw) {
+    k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float2* __restrict__ scratch, float kf,
+                       int deconv, float norm, const float2* __restrict__ tw, int* __restrict__ err) {
   extern __shared__ __align__(16) float2 sm[];
-  z_green_wide_body<N, W>(A, Gz, kf, deconv, norm, tw, blockIdx.x, blockIdx.y, sm);
+  z_green_wide_body<N, W>(A, Gz, scratch, kf, deconv, norm, tw, err, blockIdx.x, blockIdx.y, sm);
 }
+// the scratch slot of an SM belongs to one block only if two blocks cannot share the SM
+template <int N, int W>
+constexpr size_t wide_z_smem() {
+  return sizeof(float2) * (wide_z_table_offset<N, W>() + stw_size<FFTConf<N>>());
+}
+static_assert(2 * wide_z_smem<2048, 8>() > 228 * 1024, "two wide z blocks would fit on one SM");
 
 template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
@@ -232,12 +238,14 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
       k_fft_y_fwd_wide<N, WW><<<grid, NT, smem, st>>>(A, tw);
       COLA_LAUNCH_CHECK();
     }
-    // 3. z pass with the Green's function
+    // 3. z pass with the Green's function; its scratch slots sit at the start of Gy, which the
+    // inverse y passes write only afterwards
     {
-      const size_t smem = sizeof(float2) * (wide_z_table_offset<N, WW>() + stw_size<FFTConf<N>>());
+      static_assert((int64_t)kZScratchSlots * N * WW <= (int64_t)N * N * half_pitch<N>(), "scratch exceeds Gy");
+      const size_t smem = wide_z_smem<N, WW>();
       if ((rc = set_smem(k_fft_z_green_wide<N, WW>, smem))) return rc;
       LaunchScope ls_(flabel<N>(1), st);
-      k_fft_z_green_wide<N, WW><<<grid, NT, smem, st>>>(A, Gz, kf, deconv, norm, tw);
+      k_fft_z_green_wide<N, WW><<<grid, NT, smem, st>>>(A, Gz, Gy, kf, deconv, norm, tw, err);
       COLA_LAUNCH_CHECK();
     }
     // 4. inverse y passes
