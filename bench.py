@@ -795,7 +795,7 @@ def ensemble_timing(args, dev, rank, world):
             "sequential_single_box": {"value": updates / (ms_seq * 1e-3), "ms_per_step": ms_seq},
             "speedup_vs_sequential": ms_seq / ms_ens,
             "tuning": {"threads": best.threads, "tile_shape": best.tile_shape, "blocks_per_sm": best.blocks_per_sm,
-                       "radix": best.radix, "launch": best.launch},
+                       "radix": best.radix, "launch": best.launch, "mesh_streams": best.mesh_streams},
             "tune_candidates_ms": [round(float(x), 4) for x in tune_ms],
             "step": "noise + 2LPT IC + 11 force evaluations (CUDA graph per step) + density + P(k), all boxes",
             "kernels": {k_: {kk_: (round(vv_, 5) if isinstance(vv_, float) else vv_) for kk_, vv_ in kv.items()}

@@ -289,16 +289,24 @@ typedef struct cola_ensemble cola_ensemble;
  *                launches, the boxes dealt round-robin over that many streams forked inside
  *                the step graph, one box after another on each (threads, tile_shape,
  *                blocks_per_sm and radix are then unused; the results equal the single-box
- *                ones bit for bit).  Either way each step is replayed from a CUDA graph. */
+ *                ones bit for bit).  Either way each step is replayed from a CUDA graph.
+ *  mesh_streams  launch 0 only: 0 = the mesh passes as multi-box kernels too; 1, 2 or 4 =
+ *                hybrid: the binning (keys, scan, scatter), the gather and the kick/drift stay
+ *                multi-box launches for all boxes, and each box runs its own single-box mesh
+ *                passes (deposit + x r2c .. inverse x) from the ensemble's records, the boxes
+ *                dealt round-robin over that many streams forked inside the step graph (the
+ *                bins then follow each box's plan; the results equal the single-box ones bit
+ *                for bit). */
 typedef struct {
   int32_t threads;
   int32_t tile_shape;
   int32_t blocks_per_sm;
   int32_t radix;
   int32_t launch;
+  int32_t mesh_streams;
 } cola_ensemble_tuning;
 
-#define COLA_ENSEMBLE_TUNE_CANDIDATES 19
+#define COLA_ENSEMBLE_TUNE_CANDIDATES 25
 
 /* Create / destroy.  boxes: host array of nbox configurations (see the requirements above). */
 int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble** out);
@@ -331,14 +339,16 @@ int cola_ensemble_density(cola_ensemble* ens, const float* s, float* delta, cola
 int cola_ensemble_power(cola_ensemble* ens, const float* delta, int32_t nbins, double* k, double* pk,
                         int64_t* nmodes, cola_stream stream);
 /* Autotuner: times one force evaluation without the particle update (binning, mesh passes and
- * the gather into scratch) of all boxes at displacements s (read only) for each of the
- * COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
+ * the gather into scratch) of all boxes at displacements s (read only), replayed from a CUDA
+ * graph as the steps are (launched directly if cola_ensemble_use_graphs(ens, 0)), for each of
+ * the COLA_ENSEMBLE_TUNE_CANDIDATES launch shapes (reps timed
  * repetitions after one warm-up, CUDA events on `stream`; synchronises), keeps the fastest
  * and writes it to *best (may be NULL).  ms (may be NULL): host array receiving the mean
  * milliseconds of each candidate: first the 16 multi-box shapes (launch 0) in the order
  * threads in {128, 256} x tile_shape in {0, 1} x blocks_per_sm in {0, 2} x radix in {0, 1}
- * (radix fastest), then launch 1, 2 and 4.  Candidates with radix 0 and the per-box ones give
- * results bit-identical to the single-box runs. */
+ * (radix fastest), then launch 1, 2 and 4, then the hybrid mode with mesh_streams in {1, 2, 4}
+ * x threads in {128, 256} (threads fastest).  Candidates with radix 0, the per-box and the
+ * hybrid ones give results bit-identical to the single-box runs. */
 int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_ensemble_tuning* best, double* ms,
                        cola_stream stream);
 int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tuning);

@@ -48,7 +48,7 @@ SCHEMES = {"cola": 0, "cola_std": 1, "pm_std": 2, "cola_u1": 3}
 
 class cola_ensemble_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("radix", ctypes.c_int32), ("launch", ctypes.c_int32)]
+                ("radix", ctypes.c_int32), ("launch", ctypes.c_int32), ("mesh_streams", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -96,7 +96,7 @@ _SIGNATURES = {
     "cola_ensemble_profile": [_P, ctypes.c_int32],
     "cola_ensemble_profile_read": [_P, ctypes.c_int32, _P, _P, _P, _P],
 }
-COLA_ENSEMBLE_TUNE_CANDIDATES = 19
+COLA_ENSEMBLE_TUNE_CANDIDATES = 25
 _lib = None
 
 
@@ -551,14 +551,15 @@ class Ensemble:
 
     @property
     def tuning(self):
-        """(threads, tile_shape, blocks_per_sm, radix, launch); a shorter tuple given to the
-        setter is padded with zeros (launch 0 = the multi-box kernels)."""
+        """(threads, tile_shape, blocks_per_sm, radix, launch, mesh_streams); a shorter tuple given
+        to the setter is padded with zeros (launch 0 = the multi-box kernels, mesh_streams 0 = the
+        mesh passes multi-box too)."""
         t = cola_ensemble_get_tuning(self.handle)
-        return (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch)
+        return (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch, t.mesh_streams)
 
     @tuning.setter
     def tuning(self, value):
-        value = tuple(value) + (0,) * (5 - len(value))
+        value = tuple(value) + (0,) * (6 - len(value))
         cola_ensemble_set_tuning(self.handle, cola_ensemble_tuning(*value))
 
     def use_graphs(self, enable):

@@ -93,8 +93,15 @@ int plan_force_scratch(cola_plan* p, const float* s, cudaStream_t st) {
   int rc = force_meshes(p, s, st);
   if (rc || !p->binned_gather) return rc;
   Workspace& w = p->ws;
+  if (p->binned_gather4) return launch_gather_binned4(p->geo, w.freal, w.rec, reinterpret_cast<float4*>(w.meshA), st);
   return launch_gather_binned(p->geo, w.freal, w.rec, reinterpret_cast<float*>(w.meshA),
                               reinterpret_cast<float*>(w.meshG[1]), reinterpret_cast<float*>(w.meshG[2]), st);
+}
+
+int plan_force_passes(cola_plan* p, const uint4* rec, const int* offsets, cudaStream_t st) {
+  Workspace& w = p->ws;
+  return launch_force_passes(p->geo, p->tiles, rec, offsets, w.meshA, w.meshG[1], w.meshG[2], w.freal, p->Pg,
+                             p->cfg.box, p->cfg.deconv, w.tw_g, w.err, st);
 }
 
 }  // namespace cola

@@ -184,6 +184,9 @@ int launch_gather_kick_drift(const Geometry& g, const float* fmesh, float* s, fl
 // gather into the free half-spectrum buffers when the plan gathers in bin order): what the
 // ensemble autotuner times for the per-box launch mode
 int plan_force_scratch(cola_plan* p, const float* s, cudaStream_t st);
+// the mesh passes of plan p (deposit + x r2c .. inverse x) from bin-ordered records rec and bin
+// offsets `offsets` in the layout of p->tiles, supplied by the caller
+int plan_force_passes(cola_plan* p, const uint4* rec, const int* offsets, cudaStream_t st);
 int launch_gather_binned(const Geometry& g, const float* fmesh, const uint4* rec,
                          float* f0, float* f1, float* f2, cudaStream_t st);
 int launch_kick_drift(const Geometry& g, const float* f0, const float* f1, const float* f2, float* s, float* v,

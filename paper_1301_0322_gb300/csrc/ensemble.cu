@@ -42,7 +42,9 @@ struct BoxDesc {
   int* err;
 };
 
-enum { kEParticles, kEDeposit, kECols, kEC2r, kENumLists };
+// work lists: particles (one per thread), particles four per thread, deposit tiles, column
+// strips, inverse-x row blocks
+enum { kEParticles, kEParticles4, kEDeposit, kECols, kEC2r, kENumLists };
 enum { kKKeys, kKScatter, kKDeposit, kKYfwd, kKZgreen, kKYinv, kKC2r, kKGather, kKGatherB, kKKick, kKNum };
 
 constexpr int kEnsMaxBoxes = 4096;
@@ -60,6 +62,32 @@ __device__ __forceinline__ int find_box(const int* __restrict__ starts, int nbox
   return lo;
 }
 
+// The box of the items a block walks (blockIdx.x, + gridDim.x, ...): found once by bisection,
+// then moved forward, as the items only increase (a bisection per item costs a chain of
+// dependent loads every time).
+struct BoxCursor {
+  int b, first, end;  // box, its first item, one past its last
+  __device__ __forceinline__ BoxCursor(const int* __restrict__ starts, int nbox, int item) {
+    b = item < __ldg(starts + nbox) ? find_box(starts, nbox, item) : 0;
+    first = __ldg(starts + b);
+    end = __ldg(starts + b + 1);
+  }
+  // box of `item` (item >= every item passed before, item < the total)
+  __device__ __forceinline__ int operator()(const int* __restrict__ starts, int item) {
+    while (item >= end) {
+      ++b;
+      first = end;
+      end = __ldg(starts + b + 1);
+    }
+    return b;
+  }
+};
+
+// position of mesh size n in COLA_ENS_SIZES
+__host__ __device__ constexpr int ens_size_index(int n) {
+  return n == 64 ? 0 : n == 96 ? 1 : n == 128 ? 2 : n == 192 ? 3 : 4;
+}
+
 // rows of a deposit tile (y) for a tile of `rows` rows and its two shapes (tile_shape 0 / 1):
 // 8 -> 4x2 / 2x4, 16 -> 4x4 / 8x2, 32 -> 8x4 / 4x8, 64 -> 8x8 / 16x4, 128 -> 16x8 / 8x16
 __host__ __device__ constexpr int ens_tile_ty(int rows, int shape) {
@@ -69,16 +97,20 @@ __host__ __device__ constexpr int ens_tile_ty(int rows, int shape) {
 }
 
 // ---- persistent kernels -----------------------------------------------------------------------
+// Each kernel walks the items of all boxes: boxes[0 .. nbox), item list starts[0 .. nbox].
+
+// binning, four particles per thread (keys_x4_body, scatter_x4_body)
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_keys(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
                                               int nbox, const float* __restrict__ s, int* __restrict__ keys,
                                               int* __restrict__ counts) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
-    keys_body(d.g, d.tl, s + 3 * d.pbase, p, p < d.g.np3, d.bin_base, keys + d.pbase, counts, d.err);
+    const int64_t q0 = (int64_t)(item - cur.first) * NT * kPartPerThread;
+    keys_x4_body(d.g, d.tl, s + 3 * d.pbase, q0, d.bin_base, keys + d.pbase, counts, d.err);
   }
 }
 
@@ -88,11 +120,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_scatter(const BoxDesc* __rest
                                                            const float* __restrict__ s, const int* __restrict__ keys,
                                                            int* __restrict__ cursor, uint4* __restrict__ rec) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
-    scatter_body(d.g, s + 3 * d.pbase, p, p < d.g.np3, keys + d.pbase, cursor, rec);
+    const int64_t q0 = (int64_t)(item - cur.first) * NT * kPartPerThread;
+    scatter_x4_body(d.g, s + 3 * d.pbase, q0, keys + d.pbase, cursor, rec);
   }
 }
 
@@ -124,10 +157,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __rest
                                                            const uint4* __restrict__ rec,
                                                            const int* __restrict__ offsets) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc* d = boxes + b;
-    const int local = item - __ldg(starts + b);
+    const int local = item - cur.first;
     const int* ob = offsets + d->bin_base;
     switch (d->g.ng) {
 #define X(N)                                              \
@@ -150,10 +184,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
   extern __shared__ __align__(16) unsigned long long ens_smem[];
   float2* sm = reinterpret_cast<float2*>(ens_smem);
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int local = item - __ldg(starts + b);
+    const int local = item - cur.first;
     switch (d.g.ng) {
 #define X(N)                                                                                              \
   case N: {                                                                                               \
@@ -176,27 +211,57 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
   }
 }
 
+// Stage twiddle tables (fft.cuh) of the inverse-x transforms of every ensemble size, behind the
+// two stage buffers of ke_c2r3: ens_c2r_tab_offset(n) float2 entries from their start.
+constexpr int kEnsSizes[] = {64, 96, 128, 192, 256};
+constexpr int kEnsNumSizes = 5;
+template <int V>
+__host__ __device__ constexpr int ens_c2r_tab_size(int n) {
+  return n == 64    ? stw_size<FFTConfV<32, V>>()
+         : n == 96  ? stw_size<FFTConfV<48, V>>()
+         : n == 128 ? stw_size<FFTConfV<64, V>>()
+         : n == 192 ? stw_size<FFTConfV<96, V>>()
+                    : stw_size<FFTConfV<128, V>>();
+}
+template <int V>
+__host__ __device__ constexpr int ens_c2r_tab_offset(int n) {
+  int off = 0;
+  for (int k = 0; k < kEnsNumSizes && kEnsSizes[k] != n; ++k) off += ens_c2r_tab_size<V>(kEnsSizes[k]);
+  return off;
+}
+// base twiddle table of a box of each size (nullptr: no box of that size)
+struct EnsTw {
+  const float2* tw[kEnsNumSizes];
+};
+
 // Inverse x passes of all boxes: persistent, with the bulk copy of the next item (which may
 // belong to another box and mesh size) in flight during the transform of the current one.
 // half: float2 capacity of each of the two stage buffers.
 template <int NT, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restrict__ boxes,
-                                                        const int* __restrict__ starts, int nbox, int half,
+                                                        const int* __restrict__ starts, int nbox, int half, EnsTw tws,
                                                         int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned long long ens_smem[];
   float2* sm = reinterpret_cast<float2*>(ens_smem);
+  float2* tabs = sm + 2 * half;
   __shared__ __align__(8) uint64_t bars[2];
   const int total = __ldg(starts + nbox);
+#define X(N)                                                                                                   \
+  if (tws.tw[ens_size_index(N)])                                                                             \
+    stw_fill<FFTConfV<N / 2, V>, 2>(tabs + ens_c2r_tab_offset<V>(N), tws.tw[ens_size_index(N)], threadIdx.x, NT);
+  COLA_ENS_SIZES(X)
+#undef X
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
+  BoxCursor icur(starts, nbox, blockIdx.x), cur(starts, nbox, blockIdx.x);  // items issued / computed
   auto issue = [&](int item, int buf) {
-    const int b = find_box(starts, nbox, item);
+    const int b = icur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int local = item - __ldg(starts + b);
+    const int local = item - icur.first;
     const int rb = d.c2r_rb, n = d.g.ng;
     const int nrb = n * n / rb;
     const int comp = local / nrb;
@@ -218,9 +283,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restric
       if (next < total) mbar_wait(&bars[buf ^ 1], ((it + 1) >> 1) & 1);
       return;
     }
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int local = item - __ldg(starts + b);
+    const int local = item - cur.first;
     switch (d.g.ng) {
 #define X(N)                                                                                       \
   case N: {                                                                                        \
@@ -228,7 +293,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_c2r3(const BoxDesc* __restric
     constexpr int RB = NT / CM::T, nrb = N * N / RB;                                               \
     const int comp = local / nrb;                                                                  \
     c2r3_compute<N, RB, CM>(sm + buf * half, d.F + (int64_t)comp * N * N * N + (int64_t)(local - comp * nrb) * RB * N, \
-                        comp, d.kf, d.tw);                                                         \
+                            comp, d.kf, d.tw, SmemTw<CM>{tabs + ens_c2r_tab_offset<V>(N)});          \
   } break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -245,10 +310,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restr
                                                 const float* __restrict__ s1, const float* __restrict__ s2, int step,
                                                 int mode) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    const int64_t p = (int64_t)(item - cur.first) * NT + threadIdx.x;
     if (p < d.g.np3) {
       const int64_t o = 3 * d.pbase;
       gather_kick_drift_body(d.g, d.F, s + o, v + o, s1 + o, s2 + o, d.coef + (size_t)step * kCoef32, mode, nullptr,
@@ -260,15 +326,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather(const BoxDesc* __restr
 // Gather in bin order into each box's half-spectrum buffers (free once its force meshes exist):
 // the particles of box b hold bin positions pbase .. pbase + np^3 - 1 (the boxes' bins follow
 // one another and every particle has one bin).
+// f4: the forces go to A as one float4 per particle (every box's half spectrum holds 16 bytes per
+// particle), else as three float arrays in A, Gy and Gz.
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_gather_binned(const BoxDesc* __restrict__ boxes,
                                                                  const int* __restrict__ starts, int nbox,
-                                                                 const uint4* __restrict__ rec) {
+                                                                 const uint4* __restrict__ rec, bool f4) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int64_t q = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    const int64_t q = (int64_t)(item - cur.first) * NT + threadIdx.x;
     if (q < d.g.np3) {
       const uint4 r = __ldg(rec + d.pbase + q);
       const int64_t p = r.w;
@@ -282,9 +351,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_gather_binned(const BoxDesc* 
       }
       float f[3];
       gather_force(d.g, d.F, c, t, f);
-      reinterpret_cast<float*>(d.A)[p] = f[0];
-      reinterpret_cast<float*>(d.Gy)[p] = f[1];
-      reinterpret_cast<float*>(d.Gz)[p] = f[2];
+      if (f4) {
+        reinterpret_cast<float4*>(d.A)[p] = make_float4(f[0], f[1], f[2], 0.0f);
+      } else {
+        reinterpret_cast<float*>(d.A)[p] = f[0];
+        reinterpret_cast<float*>(d.Gy)[p] = f[1];
+        reinterpret_cast<float*>(d.Gz)[p] = f[2];
+      }
     }
   }
 }
@@ -295,16 +368,27 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_kick_drift(const BoxDesc* __r
                                                               const int* __restrict__ starts, int nbox,
                                                               float* __restrict__ s, float* __restrict__ v,
                                                               const float* __restrict__ s1,
-                                                              const float* __restrict__ s2, int step, int mode) {
+                                                              const float* __restrict__ s2, int step, int mode,
+                                                              bool f4) {
   const int total = __ldg(starts + nbox);
+  BoxCursor cur(starts, nbox, blockIdx.x);
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int b = find_box(starts, nbox, item);
+    const int b = cur(starts, item);
     const BoxDesc& d = boxes[b];
-    const int64_t p = (int64_t)(item - __ldg(starts + b)) * NT + threadIdx.x;
+    const int64_t p = (int64_t)(item - cur.first) * NT + threadIdx.x;
     if (p < d.g.np3) {
       const int64_t o = 3 * d.pbase;
-      const float f[3] = {reinterpret_cast<const float*>(d.A)[p], reinterpret_cast<const float*>(d.Gy)[p],
-                          reinterpret_cast<const float*>(d.Gz)[p]};
+      float f[3];
+      if (f4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(d.A) + p);
+        f[0] = q.x;
+        f[1] = q.y;
+        f[2] = q.z;
+      } else {
+        f[0] = reinterpret_cast<const float*>(d.A)[p];
+        f[1] = reinterpret_cast<const float*>(d.Gy)[p];
+        f[2] = reinterpret_cast<const float*>(d.Gz)[p];
+      }
       kick_drift_update(d.g, s + o, v + o, s1 + o, s2 + o, d.coef + (size_t)step * kCoef32, mode, p, f);
     }
   }
@@ -363,6 +447,7 @@ struct cola_ensemble {
   std::vector<cola_plan*> plans;
   int nbox = 0, nsteps = 0, min_ng = 0;
   bool binned_gather = true;  // every box gathers in bin order (as its single-box plan does)
+  bool gather_f4 = true;      // ... into one float4 per particle (as its single-box plan does)
   std::vector<int64_t> poff, moff;
   std::vector<size_t> plan_off;
   size_t ens_off = 0, ws_bytes = 0;
@@ -378,12 +463,14 @@ struct cola_ensemble {
   BoxDesc* d_boxes = nullptr;
   int* d_starts = nullptr;
   // current launch configuration
-  cola_ensemble_tuning tuning{256, 0, 0, 0, 0};
+  cola_ensemble_tuning tuning{256, 0, 0, 0, 0, 0};
   std::vector<BoxDesc> h_boxes;
-  std::vector<int> h_starts;
+  std::vector<int> h_starts;  // work list l at h_starts[l (nbox + 1)]
   int total_bins = 0;
   int grid[kKNum] = {};
   size_t smem[kKNum] = {};
+  int c2r_half = 0;     // float2 capacity of each inverse-x stage buffer
+  EnsTw tws{};
   int version = 0;
   int num_sms = 0;
   // graphs
@@ -420,6 +507,9 @@ struct cola_ensemble {
 namespace cola {
 namespace {
 
+// multi-box binning, gather and kick around every box's own mesh passes on forked streams
+bool hybrid(const cola_ensemble* e) { return e->tuning.launch == 0 && e->tuning.mesh_streams > 0; }
+
 template <int NT, int V>
 int kernel_attrs(cola_ensemble* e) {
   const void* fns[kKNum] = {(const void*)ke_keys<NT>,       (const void*)ke_scatter<NT>,
@@ -427,8 +517,8 @@ int kernel_attrs(cola_ensemble* e) {
                             (const void*)ke_cols<NT, 1, V>, (const void*)ke_cols<NT, 2, V>,
                             (const void*)ke_c2r3<NT, V>,    (const void*)ke_gather<NT>,
                             (const void*)ke_gather_binned<NT>, (const void*)ke_kick_drift<NT>};
-  const int lists[kKNum] = {kEParticles, kEParticles, kEDeposit,   kECols,     kECols,
-                            kECols,      kEC2r,       kEParticles, kEParticles, kEParticles};
+  const int lists[kKNum] = {kEParticles4, kEParticles4, kEDeposit,   kECols,      kECols,
+                            kECols,       kEC2r,        kEParticles, kEParticles, kEParticles};
   for (int k = 0; k < kKNum; ++k) {
     if (e->smem[k] > 227 * 1024) return fail(COLA_EUNSUPPORTED, "ensemble kernel: shared memory request too large");
     COLA_CUDA_CHECK(cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem[k]));
@@ -442,13 +532,20 @@ int kernel_attrs(cola_ensemble* e) {
   return COLA_OK;
 }
 
+// inverse-x stage twiddle tables of every ensemble size (float2 entries)
+int ens_c2r_tab_total(int v) {
+  return v ? ens_c2r_tab_offset<1>(0) : ens_c2r_tab_offset<0>(0);
+}
+
 // (re)build the box descriptions, work lists and launch shapes for e->tuning
 int configure(cola_ensemble* e, cudaStream_t st) {
   const int nt = e->tuning.threads;
   const int nb = e->nbox;
   e->h_boxes.assign(nb, BoxDesc{});
-  e->h_starts.assign((size_t)kENumLists * (nb + 1), 0);
+  std::vector<int64_t> items((size_t)nb * kENumLists);
   std::fill(e->smem, e->smem + kKNum, (size_t)0);
+  size_t c2r_buf = 0;
+  for (int k = 0; k < kEnsNumSizes; ++k) e->tws.tw[k] = nullptr;
   int bins = 0;
   for (int b = 0; b < nb; ++b) {
     cola_plan* p = e->plans[b];
@@ -458,12 +555,16 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     d.g = p->geo;
     if ((sh.ty & (sh.ty - 1)) || (sh.tz & (sh.tz - 1)))
       return fail(COLA_EUNSUPPORTED, "ensemble: deposit tile sides must be powers of two");
-    d.tl.ty = sh.ty;
-    d.tl.tz = sh.tz;
-    d.tl.nty = n / sh.ty;
-    d.tl.ntz = n / sh.tz;
-    d.tl.nbins = d.tl.nty * d.tl.ntz * 4;
-    d.tl.lband = tile_band_log2(d.tl.nty);
+    if (hybrid(e)) {
+      d.tl = p->tiles;  // the box's own mesh passes read its bins in its plan's tile layout
+    } else {
+      d.tl.ty = sh.ty;
+      d.tl.tz = sh.tz;
+      d.tl.nty = n / sh.ty;
+      d.tl.ntz = n / sh.tz;
+      d.tl.nbins = d.tl.nty * d.tl.ntz * 4;
+      d.tl.lband = tile_band_log2(d.tl.nty);
+    }
     d.P = p->Pg;
     d.deconv = p->cfg.deconv;
     d.bin_base = bins;
@@ -479,29 +580,36 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     d.tw = p->ws.tw_g;
     d.coef = p->ws.coef;
     d.err = p->ws.err;
+    if (!e->tws.tw[ens_size_index(n)]) e->tws.tw[ens_size_index(n)] = p->ws.tw_g;
     const int64_t part_items = (p->geo.np3 + nt - 1) / nt;
-    const int64_t items[kENumLists] = {part_items, (int64_t)d.tl.nty * d.tl.ntz, (int64_t)sh.nbx * n,
-                                       (int64_t)n * n / sh.RB * 3};
-    for (int l = 0; l < kENumLists; ++l) {
-      int* st_l = &e->h_starts[(size_t)l * (nb + 1)];
-      const int64_t next = (int64_t)st_l[b] + items[l];
-      if (next > 0x7fffffff) return fail(COLA_EINVAL, "ensemble: too many work items");
-      st_l[b + 1] = (int)next;
-    }
+    const int64_t part4_items = (p->geo.np3 + (int64_t)nt * kPartPerThread - 1) / ((int64_t)nt * kPartPerThread);
+    const int64_t it[kENumLists] = {part_items, part4_items, (int64_t)d.tl.nty * d.tl.ntz, (int64_t)sh.nbx * n,
+                                    (int64_t)n * n / sh.RB * 3};
+    for (int l = 0; l < kENumLists; ++l) items[(size_t)b * kENumLists + l] = it[l];
     const int M = n / 2;
     const size_t dep = sizeof(unsigned long long) * sh.rows * std::max(n, xrow_ld_host(M));
     const size_t cols = sizeof(float2) * n * sh.W;
     d.c2r_rb = sh.RB;
     d.c2r_ld = xrow_ld_host(M);
-    const size_t c2r = sizeof(float2) * 2 * sh.RB * xrow_ld_host(M);  // two stage buffers
+    c2r_buf = std::max(c2r_buf, (size_t)sh.RB * xrow_ld_host(M));
     e->smem[kKDeposit] = std::max(e->smem[kKDeposit], dep);
     e->smem[kKYfwd] = std::max(e->smem[kKYfwd], cols);
     e->smem[kKZgreen] = std::max(e->smem[kKZgreen], 2 * cols);
     e->smem[kKYinv] = std::max(e->smem[kKYinv], 2 * cols);
-    e->smem[kKC2r] = std::max(e->smem[kKC2r], c2r);
   }
   if (bins > e->max_bins_total) return fail(COLA_EINVAL, "ensemble: bin count above the workspace sizing");
   e->total_bins = bins;
+  e->c2r_half = (int)c2r_buf;  // two stage buffers, then the stage twiddle tables
+  e->smem[kKC2r] = sizeof(float2) * (2 * c2r_buf + ens_c2r_tab_total(e->tuning.radix));
+  e->h_starts.assign((size_t)kENumLists * (nb + 1), 0);
+  for (int l = 0; l < kENumLists; ++l) {
+    int* st_l = &e->h_starts[(size_t)l * (nb + 1)];
+    for (int b = 0; b < nb; ++b) {
+      const int64_t next = (int64_t)st_l[b] + items[(size_t)b * kENumLists + l];
+      if (next > 0x7fffffff) return fail(COLA_EINVAL, "ensemble: too many work items");
+      st_l[b + 1] = (int)next;
+    }
+  }
   const int v = e->tuning.radix;
   int rc = nt == 128 ? (v ? kernel_attrs<128, 1>(e) : kernel_attrs<128, 0>(e))
                      : (v ? kernel_attrs<256, 1>(e) : kernel_attrs<256, 0>(e));
@@ -517,16 +625,34 @@ int configure(cola_ensemble* e, cudaStream_t st) {
   return COLA_OK;
 }
 
-template <int NT, int V>
-int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
+// work list l on the device
+const int* work_list(const cola_ensemble* e, int l) { return e->d_starts + (size_t)l * (e->nbox + 1); }
+
+// Run per_box(b, stream) for every box with the boxes spread over K side streams, forked from
+// and joined back into `st` (inside a capture the forks become parallel graph branches; the
+// boxes use disjoint workspaces, so their work is independent).
+template <class F>
+int fork_join(cola_ensemble* e, cudaStream_t st, F&& per_box, int K = cola_ensemble::kForks) {
+  COLA_CUDA_CHECK(cudaEventRecord(e->fork_ev, st));
+  for (int k = 0; k < K; ++k) COLA_CUDA_CHECK(cudaStreamWaitEvent(e->side[k], e->fork_ev, 0));
+  int rc = COLA_OK;
+  for (int b = 0; b < e->nbox && !rc; ++b) rc = per_box(b, e->side[b % K]);
+  for (int k = 0; k < K; ++k) {  // join even after a failure: no stream may stay forked
+    const cudaError_t r1 = cudaEventRecord(e->join_ev[k], e->side[k]);
+    const cudaError_t r2 = cudaStreamWaitEvent(st, e->join_ev[k], 0);
+    if (!rc && (r1 != cudaSuccess || r2 != cudaSuccess)) rc = fail(COLA_ECUDA, "ensemble stream join failed");
+  }
+  return rc;
+}
+
+// binning of all boxes: one keys, scan and scatter launch for the whole ensemble
+template <int NT>
+int enqueue_binning(cola_ensemble* e, const float* s, cudaStream_t st) {
   const int nb = e->nbox;
-  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
-  const int* sd = e->d_starts + (size_t)kEDeposit * (nb + 1);
-  const int* sc = e->d_starts + (size_t)kECols * (nb + 1);
-  const int* sr = e->d_starts + (size_t)kEC2r * (nb + 1);
+  const int* sp4 = work_list(e, kEParticles4);
   {
     LaunchScope ls_("ens_keys", st);
-    ke_keys<NT><<<e->grid[kKKeys], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->counts);
+    ke_keys<NT><<<e->grid[kKKeys], NT, 0, st>>>(e->d_boxes, sp4, nb, s, e->keys, e->counts);
   }
   COLA_LAUNCH_CHECK();
   Tiles all{};
@@ -535,9 +661,29 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   if (rc) return rc;
   {
     LaunchScope ls_("ens_scatter", st);
-    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp, nb, s, e->keys, e->cursor, e->rec);
+    ke_scatter<NT><<<e->grid[kKScatter], NT, 0, st>>>(e->d_boxes, sp4, nb, s, e->keys, e->cursor, e->rec);
   }
   COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+// Mesh passes of all boxes: the multi-box kernels, or (hybrid) every box's own passes from the
+// ensemble's records, the boxes dealt over mesh_streams forked streams.
+template <int NT, int V>
+int enqueue_mesh_passes(cola_ensemble* e, cudaStream_t st) {
+  if (hybrid(e)) {
+    auto box_passes = [&](int b, cudaStream_t sb) {
+      return plan_force_passes(e->plans[b], e->rec, e->offsets + e->h_boxes[b].bin_base, sb);
+    };
+    if (e->tuning.mesh_streams > 1) return fork_join(e, st, box_passes, e->tuning.mesh_streams);
+    for (int b = 0; b < e->nbox; ++b)
+      if (const int rc = box_passes(b, st)) return rc;
+    return COLA_OK;
+  }
+  const int nb = e->nbox;
+  const int* sd = work_list(e, kEDeposit);
+  const int* sc = work_list(e, kECols);
+  const int* sr = work_list(e, kEC2r);
   {
     LaunchScope ls_("ens_deposit_fftx", st);
     ke_deposit<NT, V><<<e->grid[kKDeposit], NT, e->smem[kKDeposit], st>>>(e->d_boxes, sd, nb, e->rec, e->offsets);
@@ -560,8 +706,19 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
   COLA_LAUNCH_CHECK();
   {
     LaunchScope ls_("ens_fft_x_c2r3", st);
-    const int half = (int)(e->smem[kKC2r] / (2 * sizeof(float2)));
-    ke_c2r3<NT, V><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb, half, e->plans[0]->ws.err);
+    ke_c2r3<NT, V><<<e->grid[kKC2r], NT, e->smem[kKC2r], st>>>(e->d_boxes, sr, nb, e->c2r_half, e->tws,
+                                                              e->plans[0]->ws.err);
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+template <int NT>
+int enqueue_gather_binned(cola_ensemble* e, cudaStream_t st) {
+  {
+    LaunchScope ls_("ens_gather_binned", st);
+    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, work_list(e, kEParticles), e->nbox, e->rec,
+                                                            e->gather_f4);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
@@ -569,25 +726,24 @@ int enqueue_mesh_passes(cola_ensemble* e, const float* s, cudaStream_t st) {
 
 template <int NT, int V>
 int enqueue_step(cola_ensemble* e, int step, float* s, float* v, const float* s1, const float* s2, cudaStream_t st) {
-  int rc = enqueue_mesh_passes<NT, V>(e, s, st);
+  int rc = enqueue_binning<NT>(e, s, st);
+  if (!rc) rc = enqueue_mesh_passes<NT, V>(e, st);
   if (rc) return rc;
   const int nb = e->nbox;
-  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
+  const int* sp = work_list(e, kEParticles);
   const int mode = step == e->nsteps ? 1 : 0;
   if (!e->binned_gather) {
-    LaunchScope ls_("ens_gather_kick_drift", st);
-    ke_gather<NT><<<e->grid[kKGather], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
+    {
+      LaunchScope ls_("ens_gather_kick_drift", st);
+      ke_gather<NT><<<e->grid[kKGather], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
+    }
     COLA_LAUNCH_CHECK();
     return COLA_OK;
   }
-  {
-    LaunchScope ls_("ens_gather_binned", st);
-    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->rec);
-  }
-  COLA_LAUNCH_CHECK();
+  if ((rc = enqueue_gather_binned<NT>(e, st))) return rc;
   {
     LaunchScope ls_("ens_kick_drift", st);
-    ke_kick_drift<NT><<<e->grid[kKKick], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode);
+    ke_kick_drift<NT><<<e->grid[kKKick], NT, 0, st>>>(e->d_boxes, sp, nb, s, v, s1, s2, step, mode, e->gather_f4);
   }
   COLA_LAUNCH_CHECK();
   return COLA_OK;
@@ -606,16 +762,10 @@ int enqueue_step_any(cola_ensemble* e, int step, float* s, float* v, const float
 // writes only the half-spectrum buffers, so the particle state is left untouched).
 template <int NT, int V>
 int enqueue_force(cola_ensemble* e, const float* s, cudaStream_t st) {
-  int rc = enqueue_mesh_passes<NT, V>(e, s, st);
+  int rc = enqueue_binning<NT>(e, s, st);
+  if (!rc) rc = enqueue_mesh_passes<NT, V>(e, st);
   if (rc || !e->binned_gather) return rc;
-  const int nb = e->nbox;
-  const int* sp = e->d_starts + (size_t)kEParticles * (nb + 1);
-  {
-    LaunchScope ls_("ens_gather_binned", st);
-    ke_gather_binned<NT><<<e->grid[kKGatherB], NT, 0, st>>>(e->d_boxes, sp, nb, e->rec);
-  }
-  COLA_LAUNCH_CHECK();
-  return COLA_OK;
+  return enqueue_gather_binned<NT>(e, st);
 }
 
 int enqueue_force_any(cola_ensemble* e, const float* s, cudaStream_t st) {
@@ -633,7 +783,8 @@ int check_ens(const cola_ensemble* e) {
 bool valid_tuning(const cola_ensemble_tuning& t) {
   return (t.threads == 128 || t.threads == 256) && (t.tile_shape == 0 || t.tile_shape == 1) &&
          (t.radix == 0 || t.radix == 1) && t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64 &&
-         (t.launch == 0 || t.launch == 1 || t.launch == 2 || t.launch == 4);
+         (t.launch == 0 || t.launch == 1 || t.launch == 2 || t.launch == 4) &&
+         (t.mesh_streams == 0 || t.mesh_streams == 1 || t.mesh_streams == 2 || t.mesh_streams == 4);
 }
 
 // Run `enqueue` on `st`: directly (graphs off or profiling), or as a CUDA graph recorded on
@@ -679,23 +830,6 @@ int replay(cola_ensemble* e, cola_ensemble::Cached& c, const std::vector<uintptr
 
 uintptr_t u(const void* p) { return reinterpret_cast<uintptr_t>(p); }
 
-// Run per_box(b, stream) for every box with the boxes spread over the side streams, forked from
-// and joined back into `st` (inside a capture the forks become parallel graph branches; the
-// boxes use disjoint workspaces, so their work is independent).
-template <class F>
-int fork_join(cola_ensemble* e, cudaStream_t st, F&& per_box, int K = cola_ensemble::kForks) {
-  COLA_CUDA_CHECK(cudaEventRecord(e->fork_ev, st));
-  for (int k = 0; k < K; ++k) COLA_CUDA_CHECK(cudaStreamWaitEvent(e->side[k], e->fork_ev, 0));
-  int rc = COLA_OK;
-  for (int b = 0; b < e->nbox && !rc; ++b) rc = per_box(b, e->side[b % K]);
-  for (int k = 0; k < K; ++k) {  // join even after a failure: no stream may stay forked
-    const cudaError_t r1 = cudaEventRecord(e->join_ev[k], e->side[k]);
-    const cudaError_t r2 = cudaStreamWaitEvent(st, e->join_ev[k], 0);
-    if (!rc && (r1 != cudaSuccess || r2 != cudaSuccess)) rc = fail(COLA_ECUDA, "ensemble stream join failed");
-  }
-  return rc;
-}
-
 }  // namespace
 }  // namespace cola
 
@@ -731,6 +865,7 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
     }
     e->plans.push_back(p);
     e->binned_gather = e->binned_gather && p->binned_gather;
+    e->gather_f4 = e->gather_f4 && p->binned_gather4;
     e->poff[b + 1] = e->poff[b] + p->geo.np3;
     e->moff[b + 1] = e->moff[b] + p->ng3;
     e->plan_off[b] = off;
@@ -739,7 +874,8 @@ int cola_ensemble_create(const cola_config* boxes, int32_t nbox, cola_ensemble**
     // most bins over the candidate launch shapes: the fewest tile rows (128 threads)
     const int n = p->geo.ng;
     const int rows = 128 / std::max(host_T(n / 2, 0), host_T(n / 2, 1));
-    max_bins += 4LL * n * n / rows;
+    // (the hybrid mode bins as the box's plan does)
+    max_bins += std::max(4LL * n * n / rows, (long long)p->tiles.nbins);
   }
   if (e->poff[nbox] >= 0x7fffffffLL || max_bins >= 0x7fffffffLL) {
     delete e;
@@ -912,7 +1048,9 @@ int cola_ensemble_get_tuning(const cola_ensemble* ens, cola_ensemble_tuning* tun
 int cola_ensemble_set_tuning(cola_ensemble* ens, const cola_ensemble_tuning* tuning, cola_stream stream) {
   int rc = check_ens(ens);
   if (rc) return rc;
-  if (!tuning || !valid_tuning(*tuning)) return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape and radix 0 or 1, blocks_per_sm 0..64, launch 0, 1, 2 or 4");
+  if (!tuning || !valid_tuning(*tuning))
+    return fail(COLA_EINVAL, "tuning: threads 128 or 256, tile_shape and radix 0 or 1, blocks_per_sm 0..64, "
+                             "launch 0, 1, 2 or 4, mesh_streams 0, 1, 2 or 4");
   const cola_ensemble_tuning old = ens->tuning;
   ens->tuning = *tuning;
   if ((rc = configure(ens, (cudaStream_t)stream))) {
@@ -938,31 +1076,59 @@ int cola_ensemble_tune(cola_ensemble* ens, const float* s, int32_t reps, cola_en
   double best_ms = 1e300;
   ProfilerGuard pg(nullptr);
   // one force evaluation of all boxes without the particle update, in the candidate's mode
-  auto force = [&]() -> int {
-    if (ens->tuning.launch == 0) return enqueue_force_any(ens, s, st);
+  auto force = [&](cudaStream_t fs) -> int {
+    if (ens->tuning.launch == 0) return enqueue_force_any(ens, s, fs);
     auto box_force = [&](int b, cudaStream_t sb) { return plan_force_scratch(ens->plans[b], s + 3 * ens->poff[b], sb); };
-    if (ens->tuning.launch > 1) return fork_join(ens, st, box_force, ens->tuning.launch);
+    if (ens->tuning.launch > 1) return fork_join(ens, fs, box_force, ens->tuning.launch);
     for (int b = 0; b < ens->nbox; ++b)
-      if (const int r = box_force(b, st)) return r;
+      if (const int r = box_force(b, fs)) return r;
     return COLA_OK;
   };
   for (int i = 0; i < COLA_ENSEMBLE_TUNE_CANDIDATES && !rc; ++i) {
-    ens->tuning = i < 16 ? cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1, 0}
-                         : cola_ensemble_tuning{128, 0, 0, 0, 1 << (i - 16)};
+    ens->tuning = i < 16   ? cola_ensemble_tuning{(i & 8) ? 256 : 128, (i >> 2) & 1, (i & 2) ? 2 : 0, i & 1, 0, 0}
+                  : i < 19 ? cola_ensemble_tuning{128, 0, 0, 0, 1 << (i - 16), 0}
+                           : cola_ensemble_tuning{(i - 19) & 1 ? 256 : 128, 0, 0, 0, 0, 1 << ((i - 19) >> 1)};
     if ((rc = configure(ens, st))) break;
-    if ((rc = force())) break;  // warm-up
-    if (cudaEventRecord(e0, st) != cudaSuccess) {
-      rc = fail(COLA_ECUDA, "event record");
-      break;
+    // timed as the steps run: replayed from a CUDA graph (or launched directly with graphs off)
+    cudaGraphExec_t exec = nullptr;
+    if (ens->use_graphs) {
+      const unsigned long long before = g_launches.load();
+      if (cudaStreamBeginCapture(ens->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        rc = fail(COLA_ECUDA, "tuner: graph capture");
+        break;
+      }
+      const int frc = force(ens->cap);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ens->cap, &graph);
+      g_launches.fetch_sub(g_launches.load() - before);  // not launched yet
+      if (frc || ce != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        rc = frc ? frc : fail(COLA_ECUDA, std::string("tuner: graph capture: ") + cudaGetErrorString(ce));
+        break;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        rc = fail(COLA_ECUDA, std::string("tuner: graph instantiate: ") + cudaGetErrorString(ie));
+        break;
+      }
     }
-    for (int r = 0; r < reps && !rc; ++r) rc = force();
-    if (rc) break;
+    auto run = [&]() -> int {
+      if (!exec) return force(st);
+      return cudaGraphLaunch(exec, st) == cudaSuccess ? (int)COLA_OK : fail(COLA_ECUDA, "tuner: graph launch");
+    };
+    rc = run();  // warm-up
+    if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(COLA_ECUDA, "event record");
+    for (int r = 0; r < reps && !rc; ++r) rc = run();
     float el = 0.f;
-    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) {
+    if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
       rc = fail(COLA_ECUDA, "event timing");
-      break;
+    if (exec) {
+      cudaStreamSynchronize(st);
+      cudaGraphExecDestroy(exec);
     }
+    if (rc) break;
     const double t = (double)el / reps;
     if (ms) ms[i] = t;
     if (t < best_ms) {

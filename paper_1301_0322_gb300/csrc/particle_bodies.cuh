@@ -91,6 +91,73 @@ __device__ __forceinline__ void scatter_body(const Geometry& g, const float* __r
   place_record(key, live, r, cursor, rec);
 }
 
+// Four particles per thread in warp-strided rounds: the block of nt threads takes the 4 nt
+// particles from q0, warp w the 128 from q0 + 128 w, lane l of it the particles 32 u + l
+// (u = 0..3).  All four loads of a thread are in flight together (four times the bytes of one
+// particle per thread, which leaves these kernels bound by memory latency), and each round u
+// still covers 32 consecutive particles: as few distinct keys per warp as one particle per
+// thread, and the records of a bin stay in lattice order within each warp.
+constexpr int kPartPerThread = 4;
+__device__ __forceinline__ int64_t x4_first(int64_t q0) {
+  return q0 + (int64_t)(threadIdx.x & ~31) * kPartPerThread + (threadIdx.x & 31);
+}
+
+// keys (plus bin_base) and bin counts of the particles of this thread (see x4_first)
+__device__ __forceinline__ void keys_x4_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s,
+                                             int64_t q0, int bin_base, int* __restrict__ keys,
+                                             int* __restrict__ counts, int* __restrict__ err) {
+  constexpr int U = kPartPerThread;
+  const int64_t p0 = x4_first(q0);
+  float sx[U], sy[U], sz[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    if (p < g.np3) {
+      sx[u] = __ldg(s + p);
+      sy[u] = __ldg(s + g.np3 + p);
+      sz[u] = __ldg(s + 2 * g.np3 + p);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    const bool live = p < g.np3;
+    int key = -1;
+    if (live) {
+      key = bin_base + particle_key(g, tl, p, sx[u], sy[u], sz[u], err);
+      keys[p] = key;
+    }
+    count_key(key, live, counts);
+  }
+}
+
+// records of the particles of this thread into their bins (see x4_first)
+__device__ __forceinline__ void scatter_x4_body(const Geometry& g, const float* __restrict__ s, int64_t q0,
+                                                const int* __restrict__ keys, int* __restrict__ cursor,
+                                                uint4* __restrict__ rec) {
+  constexpr int U = kPartPerThread;
+  const int64_t p0 = x4_first(q0);
+  int k[U];
+  float sx[U], sy[U], sz[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    k[u] = -1;
+    if (p < g.np3) {
+      k[u] = __ldg(keys + p);
+      sx[u] = __ldg(s + p);
+      sy[u] = __ldg(s + g.np3 + p);
+      sz[u] = __ldg(s + 2 * g.np3 + p);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = p0 + 32 * u;
+    const bool live = p < g.np3;
+    place_record(k[u], live, live ? particle_record(g, p, sx[u], sy[u], sz[u]) : uint4{}, cursor, rec);
+  }
+}
+
 // CIC gather of the three force meshes fmesh [3][ng^3] for a cloud that starts at cells c with
 // upper-neighbour weights t / 2^F (the deposit's weights).
 __device__ __forceinline__ void gather_force(const Geometry& g, const float* __restrict__ fmesh, const int (&c)[3],

@@ -13,37 +13,11 @@
 namespace cola {
 
 // ---- binning -------------------------------------------------------------------------------
-// Four particles per thread: a warp takes 128 consecutive particles, lane l the particles
-// 32 u + l (u = 0..3), whose loads are all in flight together: four times the bytes in flight
-// per thread of k_keys (bound by memory latency at one particle per thread), while every round
-// u still covers 32 consecutive particles (as few distinct keys per warp as k_keys).
-constexpr int kPartPerThread = 4;
+// four particles per thread (keys_x4_body)
 __global__ void __launch_bounds__(256) k_keys_x4(Geometry g, Tiles tl, const float* __restrict__ s,
                                                  int* __restrict__ keys, int* __restrict__ counts,
                                                  int* __restrict__ err) {
-  constexpr int U = kPartPerThread;
-  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U + (threadIdx.x & 31);
-  float sx[U], sy[U], sz[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int64_t p = p0 + 32 * u;
-    if (p < g.np3) {
-      sx[u] = __ldg(s + p);
-      sy[u] = __ldg(s + g.np3 + p);
-      sz[u] = __ldg(s + 2 * g.np3 + p);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int64_t p = p0 + 32 * u;
-    const bool live = p < g.np3;
-    int key = -1;
-    if (live) {
-      key = particle_key(g, tl, p, sx[u], sy[u], sz[u], err);
-      keys[p] = key;
-    }
-    count_key(key, live, counts);
-  }
+  keys_x4_body(g, tl, s, (int64_t)blockIdx.x * blockDim.x * kPartPerThread, 0, keys, counts, err);
 }
 
 // Exclusive scan of the bin counts in three launches (block sums, scan of the block sums,
@@ -110,32 +84,11 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int n, int* __restrict__ co
   if (i == n - 1) offsets[n] = excl + x;
 }
 
-// four particles per thread, as k_keys_x4 (round u places 32 consecutive particles: a bin's
-// records stay in lattice order within each warp)
+// four particles per thread (scatter_x4_body)
 __global__ void __launch_bounds__(256) k_scatter_x4(Geometry g, const float* __restrict__ s,
                                                     const int* __restrict__ keys, int* __restrict__ cursor,
                                                     uint4* __restrict__ rec) {
-  constexpr int U = kPartPerThread;
-  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U + (threadIdx.x & 31);
-  int k[U];
-  float sx[U], sy[U], sz[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int64_t p = p0 + 32 * u;
-    k[u] = -1;
-    if (p < g.np3) {
-      k[u] = __ldg(keys + p);
-      sx[u] = __ldg(s + p);
-      sy[u] = __ldg(s + g.np3 + p);
-      sz[u] = __ldg(s + 2 * g.np3 + p);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int64_t p = p0 + 32 * u;
-    const bool live = p < g.np3;
-    place_record(k[u], live, live ? particle_record(g, p, sx[u], sy[u], sz[u]) : uint4{}, cursor, rec);
-  }
+  scatter_x4_body(g, s, (int64_t)blockIdx.x * blockDim.x * kPartPerThread, keys, cursor, rec);
 }
 
 // ---- deposit ----------------------------------------------------------------------------------

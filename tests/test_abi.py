@@ -145,8 +145,8 @@ def test_ensemble_create_validates_and_lays_out_the_boxes(lib):
         cdll = lib.load_library()
         assert cdll.cola_ensemble_step(h, 0, None, None, None, None, None) == 5  # COLA_ENOWORKSPACE
         t = lib.cola_ensemble_get_tuning(h)
-        assert (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch) == (256, 0, 0, 0, 0)
-        assert lib.COLA_ENSEMBLE_TUNE_CANDIDATES == 19
+        assert (t.threads, t.tile_shape, t.blocks_per_sm, t.radix, t.launch, t.mesh_streams) == (256, 0, 0, 0, 0, 0)
+        assert lib.COLA_ENSEMBLE_TUNE_CANDIDATES == 25
     finally:
         lib.cola_ensemble_destroy(h)
     with pytest.raises(lib.ColaError) as e:

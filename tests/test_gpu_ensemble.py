@@ -93,7 +93,7 @@ def test_every_launch_shape_gives_the_same_result(ens, threads, tile_shape, bloc
     ens.tuning = (256, 0, 0, 0)
     ref_s, ref_v = run_steps(ens, SEEDS, 2)
     ens.tuning = (threads, tile_shape, blocks_per_sm, radix)
-    assert ens.tuning == (threads, tile_shape, blocks_per_sm, radix, 0)
+    assert ens.tuning == (threads, tile_shape, blocks_per_sm, radix, 0, 0)
     s, v = run_steps(ens, SEEDS, 2)
     ens.status()
     if radix == 0:
@@ -111,7 +111,25 @@ def test_per_box_launch_mode_gives_the_same_result(ens, streams):
     ens.tuning = (256, 0, 0, 0)
     ref_s, ref_v = run_steps(ens, SEEDS, 2)
     ens.tuning = (128, 0, 0, 0, streams)
-    assert ens.tuning == (128, 0, 0, 0, streams)
+    assert ens.tuning == (128, 0, 0, 0, streams, 0)
+    for graphs in (True, False):
+        ens.use_graphs(graphs)
+        s, v = run_steps(ens, SEEDS, 2)
+        ens.status()
+        assert torch.equal(s, ref_s) and torch.equal(v, ref_v)
+    ens.use_graphs(True)
+    ens.tuning = (256, 0, 0, 0)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+@pytest.mark.parametrize("mesh_streams", [1, 2, 4])
+def test_hybrid_mode_gives_the_same_result(ens, threads, mesh_streams):
+    # multi-box binning, gather and kick around every box's own single-box mesh passes (on 1, 2
+    # or 4 forked streams): the boxes bin as their plans do, so the result is bit-identical
+    ens.tuning = (256, 0, 0, 0)
+    ref_s, ref_v = run_steps(ens, SEEDS, 2)
+    ens.tuning = (threads, 0, 0, 0, 0, mesh_streams)
+    assert ens.tuning == (threads, 0, 0, 0, 0, mesh_streams)
     for graphs in (True, False):
         ens.use_graphs(graphs)
         s, v = run_steps(ens, SEEDS, 2)
@@ -133,11 +151,13 @@ def test_graph_replay_equals_direct_launches(cola, ens):
     assert torch.equal(s_g2, s_e) and torch.equal(v_g2, v_e)
 
 
-@pytest.mark.parametrize("launch,per_step", [(0, 12), (1, 12 * len(BOXES)), (2, 12 * len(BOXES))])
-def test_graph_replay_launch_count_per_step(cola, ens, launch, per_step):
+@pytest.mark.parametrize("launch,mesh_streams,per_step",
+                         [(0, 0, 12), (0, 2, 7 + 5 * len(BOXES)), (1, 0, 12 * len(BOXES)), (2, 0, 12 * len(BOXES))])
+def test_graph_replay_launch_count_per_step(cola, ens, launch, mesh_streams, per_step):
     # keys, three scan passes, scatter, deposit + x r2c, forward y, z + Green, inverse y,
-    # inverse x, gather in bin order, kick/drift: once for all boxes (launch 0) or per box (1)
-    ens.tuning = (256, 0, 0, 0, launch)
+    # inverse x, gather in bin order, kick/drift: once for all boxes (launch 0), per box (launch
+    # 1, 2), or the five mesh passes per box and the rest once (hybrid)
+    ens.tuning = (256, 0, 0, 0, launch, mesh_streams)
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     ens.step(0, s, v, s1, s2)  # records the graph for these pointers
     torch.cuda.synchronize()
@@ -154,10 +174,11 @@ def test_graph_replay_launch_count_per_step(cola, ens, launch, per_step):
 def test_autotuner_picks_the_fastest_candidate(cola, ens):
     s, v, s1, s2 = ens.ic_2lpt(ens.noise(SEEDS))
     best, ms = ens.tune(s, reps=2)
-    assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix, best.launch) == ens.tuning
-    assert np.all(ms > 0) and len(ms) == 19
-    order = [(t, sh, b, r, 0) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
-    order += [(128, 0, 0, 0, 1), (128, 0, 0, 0, 2), (128, 0, 0, 0, 4)]
+    assert (best.threads, best.tile_shape, best.blocks_per_sm, best.radix, best.launch, best.mesh_streams) == ens.tuning
+    assert np.all(ms > 0) and len(ms) == 25
+    order = [(t, sh, b, r, 0, 0) for t in (128, 256) for sh in (0, 1) for b in (0, 2) for r in (0, 1)]
+    order += [(128, 0, 0, 0, 1, 0), (128, 0, 0, 0, 2, 0), (128, 0, 0, 0, 4, 0)]
+    order += [(t, 0, 0, 0, 0, m) for m in (1, 2, 4) for t in (128, 256)]
     assert order[int(np.argmin(ms))] == ens.tuning
     ens.status()
 
