@@ -54,7 +54,7 @@ __global__ void k_lambda_deposit(Geometry g, const float* __restrict__ s, const 
   fixed_axis(g, ix, s[p], c[0], t[0]);
   fixed_axis(g, iy, s[n3 + p], c[1], t[1]);
   fixed_axis(g, iz, s[2 * n3 + p], c[2], t[2]);
-  const float inv_one = 1.0f / (float)(1 << g.fbits);
+  const float inv_one = __int_as_float((127 - g.fbits) << 23);  // 2^-F from its bit pattern
   float w1[3], w0[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_gather_adjoint(Geometry g, const float*
   fixed_axis(g, ix, s[p], c[0], t[0]);
   fixed_axis(g, iy, s[n3 + p], c[1], t[1]);
   fixed_axis(g, iz, s[2 * n3 + p], c[2], t[2]);
-  const float inv_one = 1.0f / (float)(1 << g.fbits);
+  const float inv_one = __int_as_float((127 - g.fbits) << 23);  // 2^-F from its bit pattern
   float w1[3], w0[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {

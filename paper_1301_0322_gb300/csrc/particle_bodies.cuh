@@ -164,7 +164,7 @@ __device__ __forceinline__ void gather_force(const Geometry& g, const float* __r
                                              const int (&t)[3], float (&f)[3]) {
   const int ng = g.ng;
   const int64_t ng3 = (int64_t)ng * ng * ng;
-  const float inv_one = 1.0f / (float)(1 << g.fbits);
+  const float inv_one = __int_as_float((127 - g.fbits) << 23);  // 2^-F from its bit pattern
   float w1[3], w0[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {

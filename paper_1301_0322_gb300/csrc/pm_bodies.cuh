@@ -356,6 +356,10 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
     const float sv = n < N ? sinc_pi_f(signed_mode(n, N), N) : sinc_pi_f(bx * W + (n - N), N);
     (n < N ? sz2[n] : sx2[n - N]) = sv * sv;
   }
+  // the slot still holds the previous block's strip, dead now: drop its lines from L2 rather
+  // than let them be written back (the barrier orders this before the slot's new writes)
+  for (int l = threadIdx.x; l < N * W * (int)sizeof(float2) / 128; l += NT)
+    discard_l2_line(reinterpret_cast<char*>(sc) + 128 * l);
   __syncthreads();
   auto mem = [&](int n) -> float2& { return S[n * W + w]; };
   {

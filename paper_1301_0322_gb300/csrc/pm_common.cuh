@@ -34,7 +34,8 @@ __device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, in
   const int64_t period = (int64_t)g.ng << g.fbits;
   const int64_t q = g.ratio ? ((int64_t)i * g.ratio) << g.fbits : (((int64_t)i * g.ng) << g.fbits) / g.np;
   const float w = __fmul_rn(s, g.scale32);
-  const float ws = __fmul_rn(w, (float)one);  // exact: power-of-two scaling
+  // 2^F from its bit pattern (no 64-bit integer conversion); exact power-of-two scaling
+  const float ws = __fmul_rn(w, __int_as_float((127 + g.fbits) << 23));
   int64_t f;
   if (fabsf(ws) < 4194304.0f) {
     // floor(ws) for |ws| < 2^22 without a conversion instruction: ws + 1.5 2^23 rounded down

@@ -62,5 +62,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 // Prefetch the L2 line holding `p` (a hint; no completion to wait for).
 __device__ __forceinline__ void prefetch_l2_line(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// drop the 128-byte L2 line at p (128-byte aligned) without writing it back: for scratch that
+// is dead until its next writer overwrites it whole
+__device__ __forceinline__ void discard_l2_line(void* p) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory"); }
 
 }  // namespace cola
