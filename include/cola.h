@@ -184,6 +184,15 @@ int cola_density(cola_plan* plan, const float* s, int64_t* rho_fix, float* delta
 int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, double* pk,
                int64_t* nmodes, cola_stream stream);
 
+/* The power spectrum of cola_power of the CIC density of cola_density at displacements s (Sec.
+ * 3.1), without a caller-owned mesh: the density and its transform go to the plan's force
+ * meshes, which hold nothing between calls that write them (the next force evaluation rebuilds
+ * them).  The same kernels as cola_density + cola_power, so the same k, pk, nmodes bit for bit.
+ * s: device float32 [3][np^3] (read only); k, pk: device float64 [nbins]; nmodes: device int64
+ * [nbins]; nbins <= ng. */
+int cola_density_power(cola_plan* plan, const float* s, int32_t nbins, double* k, double* pk, int64_t* nmodes,
+                       cola_stream stream);
+
 /* Cross-correlation of two density meshes (Sec. 3.1) and n_max (eq. nmax, App. B), for
  * comparing a run with a reference run of the same initial conditions.  Per shell
  * b = 1..nbins (the shells and weights of cola_power): k, P_a and P_b as cola_power,

@@ -10,7 +10,7 @@ from .cola import (COLA_NCOEF, ColaDensity, ColaError, Ensemble, Plan, cola_coef
                    cola_ensemble_noise, cola_ensemble_ic_2lpt, cola_ensemble_step, cola_ensemble_density,
                    cola_ensemble_power, cola_ensemble_tune, cola_ensemble_get_tuning, cola_ensemble_set_tuning,
                    cola_ensemble_use_graphs, cola_ensemble_status, cola_cross_power, cola_fof,
-                   cola_set_fof_union_tries)
+                   cola_set_fof_union_tries, cola_density_power)
 
 __all__ = ["Plan", "Ensemble", "ColaError", "ColaDensity", "COLA_NCOEF", "load_library", "cola_config_default",
            "cola_plan_create", "cola_plan_destroy", "cola_workspace_bytes", "cola_set_workspace", "cola_coeffs",
@@ -21,4 +21,4 @@ __all__ = ["Plan", "Ensemble", "ColaError", "ColaDensity", "COLA_NCOEF", "load_l
            "cola_ensemble_noise", "cola_ensemble_ic_2lpt", "cola_ensemble_step", "cola_ensemble_density",
            "cola_ensemble_power", "cola_ensemble_tune", "cola_ensemble_get_tuning", "cola_ensemble_set_tuning",
            "cola_ensemble_use_graphs", "cola_ensemble_status", "cola_cross_power", "cola_fof",
-           "cola_set_fof_union_tries"]
+           "cola_set_fof_union_tries", "cola_density_power"]

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "cola_force": [_P, _P, _P, _P],
     "cola_density": [_P, _P, _P, _P, _P],
     "cola_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
+    "cola_density_power": [_P, _P, ctypes.c_int32, _P, _P, _P, _P],
     "cola_fft_r2c": [_P, ctypes.c_int32, _P, _P, _P],
     "cola_cross_power": [_P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P],
     "cola_fof": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P],
@@ -195,6 +196,11 @@ def cola_density(h, s, rho_fix, delta, stream=None):
 
 def cola_power(h, delta, nbins, k, pk, nmodes, stream=None):
     _check(load_library().cola_power(h, _ptr(delta), int(nbins), _ptr(k), _ptr(pk), _ptr(nmodes), _stream(stream)))
+
+
+def cola_density_power(h, s, nbins, k, pk, nmodes, stream=None):
+    _check(load_library().cola_density_power(h, _ptr(s), int(nbins), _ptr(k), _ptr(pk), _ptr(nmodes),
+                                             _stream(stream)))
 
 
 def cola_power_noalloc(delta, ng, box, nbins, k, pk, nmodes, stream=None):
@@ -396,6 +402,16 @@ class Plan:
         pk = self._empty(nbins, torch.float64)
         nm = self._empty(nbins, torch.int64)
         cola_power(self.handle, delta, nbins, k, pk, nm)
+        return k, pk, nm
+
+    def density_power(self, s, nbins):
+        """(k, P, nmodes) of the CIC density at displacements s, with no density mesh of the
+        caller's (the plan's force meshes serve as scratch); equal to power(density(s)[1])."""
+        _expect(s, torch.float32, 3 * self.n3, "s")
+        k = self._empty(nbins, torch.float64)
+        pk = self._empty(nbins, torch.float64)
+        nm = self._empty(nbins, torch.int64)
+        cola_density_power(self.handle, s, nbins, k, pk, nm)
         return k, pk, nm
 
     def cross_power(self, delta_a, delta_b, nbins):

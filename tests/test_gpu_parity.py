@@ -183,7 +183,10 @@ def test_full_run_parity_32p_64g(cola, scheme, log_a):
     # P(k) of the final density, k < k_Nyquist / 2
     _, d = plan.density(s, rho=False)
     nb = ng // 4
-    _, p, nm = (host(t) for t in plan.power(d, nb))
+    k, p, nm = (host(t) for t in plan.power(d, nb))
+    # the same spectrum with no density mesh of the caller's: the same kernels, bit for bit
+    k2, p2, nm2 = (host(t) for t in plan.density_power(s, nb))
+    assert np.array_equal(k2, k) and np.array_equal(p2, p) and np.array_equal(nm2, nm)
     pos = np.mod(omesh.lattice_q(n_p, box) + ref["s"], box)
     dref = omesh.overdensity(omesh.cic_deposit(pos, ng, box), n_p**3)
     _, pr, nr = opower.power_spectrum(dref, box, nb)
@@ -372,7 +375,10 @@ def test_run_at_the_benchmark_resolution_tracks_the_oracle(cola):
     # response to the one-rounding perturbation is 2.4e-6 here)
     _, d = plan.density(s, rho=False)
     nb = ng // 4
-    _, p, nm = (host(t) for t in plan.power(d, nb))
+    k, p, nm = (host(t) for t in plan.power(d, nb))
+    # the same spectrum with no density mesh of the caller's: the same kernels, bit for bit
+    k2, p2, nm2 = (host(t) for t in plan.density_power(s, nb))
+    assert np.array_equal(k2, k) and np.array_equal(p2, p) and np.array_equal(nm2, nm)
     pos = np.mod(omesh.lattice_q(n_p, box) + ref["s"], box)
     dref = omesh.overdensity(omesh.cic_deposit(pos, ng, box), n_p**3)
     _, pr, nr = opower.power_spectrum(dref, box, nb)
