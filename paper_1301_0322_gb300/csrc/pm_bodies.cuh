@@ -159,7 +159,7 @@ __device__ __forceinline__ void deposit_fftx_body(const Geometry& g, const Tiles
     overflow |= ((h.x | h.y) >> 30) != 0u;
     const unsigned long long a = ((unsigned long long)h.x << 32) | l.x;
     const unsigned long long b = ((unsigned long long)h.y << 32) | l.y;
-    return make_float2(fmaf(__ull2float_rn(a), dscale, -1.0f), fmaf(__ull2float_rn(b), dscale, -1.0f));
+    return make_float2(fmaf(u64_to_f32_rn(a), dscale, -1.0f), fmaf(u64_to_f32_rn(b), dscale, -1.0f));
   };
   auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   auto store = [&](int n, float2 x) { buf[xpad<R0>(n)] = x; };

@@ -56,6 +56,19 @@ __device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, in
 
 __device__ __forceinline__ int wrap_inc(int c, int n) { return c + 1 == n ? 0 : c + 1; }
 
+// float32 nearest to v (ties to even), v < 2^62, as __ull2float_rn but with 32-bit integer and
+// float32 instructions only (a 64-bit conversion runs on the narrow float64 pipe of sm_103a):
+// with lz leading zeros in the high word, m = the 32 bits of v from its leading one down, its
+// lowest bit ORed with every bit below them (sticky); m's rounding to 24 bits is v's rounding,
+// and the scale 2^(32 - lz) is exact.
+__device__ __forceinline__ float u64_to_f32_rn(unsigned long long v) {
+  const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+  const unsigned lz = __clz(hi);                       // 32 if hi == 0
+  unsigned m = __funnelshift_lc(lo, hi, lz);           // top 32 bits of v << lz (lo when lz = 32)
+  m |= __funnelshift_lc(0u, lo, lz) != 0u ? 1u : 0u;   // bits of lo shifted out below m
+  return __fmul_rn(__uint2float_rn(m), __int_as_float((int)(127 + 32 - lz) << 23));
+}
+
 // Exact 64-bit accumulation in shared memory held as two 32-bit words per cell, the low words
 // in one array and the high words in another: the low word is added with carry detection (the
 // atomic returns the previous value; the add wrapped iff the new value is below it) and the
