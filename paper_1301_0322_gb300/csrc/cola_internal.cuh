@@ -39,6 +39,8 @@ struct Geometry {
   // division of a 32-bit index by np as a multiply-high and shifts (set_np_divider)
   uint32_t np_mul;
   int np_sh1, np_sh2;
+  // fixed_axis may take its 32-bit path: ratio != 0 and 2^22 <= ng 2^F <= 2^30
+  int fast32;
 };
 
 // Unsigned 32-bit division by an invariant d >= 1 (Granlund & Montgomery 1994, Sec. 4): with
@@ -51,6 +53,8 @@ inline void set_np_divider(Geometry& g) {
   g.np_mul = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
   g.np_sh1 = l < 1 ? l : 1;
   g.np_sh2 = l > 1 ? l - 1 : 0;
+  const int64_t period = (int64_t)g.ng << g.fbits;
+  g.fast32 = g.ratio != 0 && period >= (1LL << 22) && period <= (1LL << 30);
 }
 
 struct Tiles {

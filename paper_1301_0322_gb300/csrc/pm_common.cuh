@@ -30,16 +30,27 @@ __device__ __forceinline__ void lattice_index(const Geometry& g, int64_t p, int&
 //   f = (floor(i ng 2^F / np) + floor(fl32(s * fl32(ng/L)) * 2^F)) mod (ng 2^F)
 // returns the cell (f >> F) and the upper-neighbour weight t = f mod 2^F.
 __device__ __forceinline__ void fixed_axis(const Geometry& g, int i, float s, int& cell, int& t) {
-  const int64_t one = 1LL << g.fbits;
-  const int64_t period = (int64_t)g.ng << g.fbits;
-  const int64_t q = g.ratio ? ((int64_t)i * g.ratio) << g.fbits : (((int64_t)i * g.ng) << g.fbits) / g.np;
   const float w = __fmul_rn(s, g.scale32);
   // 2^F from its bit pattern (no 64-bit integer conversion); exact power-of-two scaling
   const float ws = __fmul_rn(w, __int_as_float((127 + g.fbits) << 23));
+  if (g.fast32 && fabsf(ws) < 4194304.0f) {
+    // the same in 32 bits: the lattice offset is below ng 2^F <= 2^30 and |floor(ws)| < 2^22 <=
+    // ng 2^F, so f lies in (-2^22, 2^30 + 2^22) and one wrap brings it into [0, ng 2^F).
+    // floor(ws) without a conversion instruction: ws + 1.5 2^23 rounded down lies in
+    // [2^23, 2^24), where floats are the integers and their bit patterns consecutive.
+    const int period = g.ng << g.fbits;
+    int f = ((i * g.ratio) << g.fbits) + (__float_as_int(__fadd_rd(ws, 12582912.0f)) - 0x4B400000);
+    if (f < 0) f += period;
+    else if (f >= period) f -= period;
+    cell = f >> g.fbits;
+    t = f & ((1 << g.fbits) - 1);
+    return;
+  }
+  const int64_t one = 1LL << g.fbits;
+  const int64_t period = (int64_t)g.ng << g.fbits;
+  const int64_t q = g.ratio ? ((int64_t)i * g.ratio) << g.fbits : (((int64_t)i * g.ng) << g.fbits) / g.np;
   int64_t f;
   if (fabsf(ws) < 4194304.0f) {
-    // floor(ws) for |ws| < 2^22 without a conversion instruction: ws + 1.5 2^23 rounded down
-    // lies in [2^23, 2^24), where floats are the integers and their bit patterns consecutive
     f = q + (int64_t)(__float_as_int(__fadd_rd(ws, 12582912.0f)) - 0x4B400000);
   } else {
     f = q + (int64_t)floorf(ws);
