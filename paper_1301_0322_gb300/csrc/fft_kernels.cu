@@ -54,12 +54,17 @@ __global__ void __launch_bounds__(FFTConf<N>::T * cols_pass_width<N>(), cols_pas
 // Real rows of length N -> half-spectrum rows (N/2 + 1 entries, stride P), via a complex
 // FFT of length M = N/2 of z[n] = x[2n] + i x[2n+1] and the split
 //   X[k] = (Z[k] + conj Z[M-k]) / 2 - (i/2) exp(-2 pi i k/N) (Z[k] - conj Z[M-k]).
+// The x passes read their stage twiddles from a shared-memory table behind the row buffers
+// (fft.cuh; filled per block, first read after the transform's first barrier).
 template <int N>
 __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
     k_fft_x_r2c(const float* __restrict__ in, float2* __restrict__ out, int P, const float2* __restrict__ tw) {
   constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
   constexpr int R0 = first_radix<FFTConf<M>>();
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stab = smem + RB * LD;
+  stw_fill<FFTConf<M>, 2>(stab, tw, threadIdx.x, T * RB);
+  const SmemTw<FFTConf<M>> stw{stab};
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = reinterpret_cast<const float2*>(in + row * N);
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
   auto load = [&](int n) -> float2 { return src[n]; };
   auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   auto store = [&](int n, float2 x) { buf[xpad<R0>(n)] = x; };
-  fft_1d<M, 2, false>(t, tw, load, mem, store);
+  fft_1d<M, 2, false>(t, stw, load, mem, store);
   __syncthreads();
   float2* dst = out + row * P;
   // X[k] = e + p and X[M - k] = conj(e - p) from one pair Z[k], Z[M - k] (p = W^k (-i d))
@@ -89,7 +94,10 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
                 float scale) {
   constexpr int M = N / 2, T = FFTConf<M>::T, RB = x_rows<N>(), LD = xrow_ld<M>();
   constexpr int R0 = first_radix<FFTConf<M>>();
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stab = smem + RB * LD;
+  stw_fill<FFTConf<M>, 2>(stab, tw, threadIdx.x, T * RB);
+  const SmemTw<FFTConf<M>> stw{stab};
   const int t = threadIdx.x % T, w = threadIdx.x / T;
   const int64_t row = (int64_t)blockIdx.x * RB + w;
   const float2* src = in + row * P;
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(FFTConf<N / 2>::T * x_rows<N>())
   auto mem = [&](int n) -> float2& { return buf[xpad<R0>(n)]; };
   float2* dst = reinterpret_cast<float2*>(out + row * N);
   auto store = [&](int n, float2 x) { dst[n] = c_scale(x, scale); };
-  fft_1d<M, 2, true>(t, tw, load, mem, store);
+  fft_1d<M, 2, true>(t, stw, load, mem, store);
 }
 
 // persistent per-size kernel labels for the profiler
@@ -127,7 +135,7 @@ static void allow_smem(K kernel, size_t bytes) {
 template <int N>
 static int x_r2c(const float* in, float2* out, int64_t nrows, int P, const float2* tw, cudaStream_t st) {
   constexpr int M = N / 2, RB = x_rows<N>();
-  const size_t smem = (size_t)RB * xrow_ld<M>() * sizeof(float2);
+  const size_t smem = (size_t)(RB * xrow_ld<M>() + stw_size<FFTConf<M>>()) * sizeof(float2);
   if (nrows % RB) return fail(COLA_EINVAL, "fft x pass: row count not a multiple of the block rows");
   allow_smem(k_fft_x_r2c<N>, smem);
   { LaunchScope ls_(label<N>("r2c"), st);
@@ -139,7 +147,7 @@ static int x_r2c(const float* in, float2* out, int64_t nrows, int P, const float
 template <int N>
 static int x_c2r(const float2* in, float* out, int64_t nrows, int P, const float2* tw, float scale, cudaStream_t st) {
   constexpr int M = N / 2, RB = x_rows<N>();
-  const size_t smem = (size_t)RB * xrow_ld<M>() * sizeof(float2);
+  const size_t smem = (size_t)(RB * xrow_ld<M>() + stw_size<FFTConf<M>>()) * sizeof(float2);
   if (nrows % RB) return fail(COLA_EINVAL, "fft x pass: row count not a multiple of the block rows");
   allow_smem(k_fft_x_c2r<N>, smem);
   { LaunchScope ls_(label<N>("c2r"), st);
