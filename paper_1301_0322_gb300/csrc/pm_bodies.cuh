@@ -320,26 +320,31 @@ __host__ __device__ constexpr int wide_z_table_offset() {
 // scratch slots of the wide z pass (one per SM id, N W float2 each)
 constexpr int kZScratchSlots = 512;
 
-// z pass with the Green's function, one exchange buffer: the forward transform of the strip
-// (Green's function applied as it is stored) goes to a scratch slot of this SM, contiguous
-// [n][w]; the inverse transforms of i k_z phi (-> Gz) and of phi (-> A) read it back from L2
-// as whole 128-byte lines (the strip itself spans N rows 16.8 MB apart at N = 2048).  One block
-// fits per SM (shared memory), so the slot of %smid is this block's alone while it runs.
+// z pass with the Green's function, one exchange buffer.  SCRATCH (one block per SM): the
+// forward transform of the strip (Green's function applied as it is stored) goes to a scratch
+// slot of this SM, contiguous [n][w]; the inverse transforms of i k_z phi (-> Gz) and of phi
+// (-> A) read it back from L2 as whole 128-byte lines (the strip itself spans N rows 16.8 MB
+// apart at N = 2048).  One block fits per SM (shared memory), so the slot of %smid is this
+// block's alone while it runs.  Without SCRATCH (two blocks per SM) phi goes to A and the
+// inverse transforms read it back from there (an L2 hit).
 // block (bx, ky): W columns kx of the slab ky (T(N) W threads); scratch: kZScratchSlots N W float2
-template <int N, int W, class C = FFTConf<N>>
+template <int N, int W, bool SCRATCH, class C = FFTConf<N>>
 __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz,
                                                   float2* __restrict__ scratch, float kf, int deconv, float norm,
                                                   const float2* __restrict__ tw, int* __restrict__ err, int bx,
                                                   int ky, float2* sm) {
   constexpr int nh = N / 2 + 1, NT = C::T * W, P = half_pitch<N>();
-  unsigned smid, nsmid;
-  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-  asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
-  if (nsmid > (unsigned)kZScratchSlots) {
-    if (threadIdx.x == 0) atomicOr(err, kErrSmIds);
-    return;
+  float2* sc = nullptr;
+  if constexpr (SCRATCH) {
+    unsigned smid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    if (nsmid > (unsigned)kZScratchSlots) {
+      if (threadIdx.x == 0) atomicOr(err, kErrSmIds);
+      return;
+    }
+    sc = scratch + (int64_t)smid * (N * W);
   }
-  float2* sc = scratch + (int64_t)smid * (N * W);
   float2* S = sm;
   float* sz2 = reinterpret_cast<float*>(sm + N * W);
   float* sx2 = sz2 + N;
@@ -356,11 +361,15 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
     const float sv = n < N ? sinc_pi_f(signed_mode(n, N), N) : sinc_pi_f(bx * W + (n - N), N);
     (n < N ? sz2[n] : sx2[n - N]) = sv * sv;
   }
-  // the slot still holds the previous block's strip, dead now: drop its lines from L2 rather
-  // than let them be written back (the barrier orders this before the slot's new writes)
-  for (int l = threadIdx.x; l < N * W * (int)sizeof(float2) / 128; l += NT)
-    discard_l2_line(reinterpret_cast<char*>(sc) + 128 * l);
+  if constexpr (SCRATCH) {
+    // the slot still holds the previous block's strip, dead now: drop its lines from L2 rather
+    // than let them be written back (the barrier orders this before the slot's new writes)
+    for (int l = threadIdx.x; l < N * W * (int)sizeof(float2) / 128; l += NT)
+      discard_l2_line(reinterpret_cast<char*>(sc) + 128 * l);
+  }
   __syncthreads();
+  // phi of element n of this thread's column: where the forward transform leaves it
+  auto phi_at = [&](int n) -> float2* { return SCRATCH ? sc + n * W + w : a + n * zstride; };
   auto mem = [&](int n) -> float2& { return S[n * W + w]; };
   {
     const int ny = signed_mode(ky, N);
@@ -380,15 +389,15 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
         }
         gk = __fdividef(norm, den);
       }
-      __stcg(sc + n * W + w, c_scale(x, gk));
+      if (SCRATCH || valid) __stcg(phi_at(n), c_scale(x, gk));
     };
     fft_1d<N, 1, false, C>(t, stw, load, mem, store);
   }
-  __syncthreads();  // phi of the strip is in the scratch slot (visible to the block after the barrier)
+  __syncthreads();  // phi of the strip is in the scratch slot or in A (visible to the block after the barrier)
   {
     auto load = [&](int n) -> float2 {
       const float kz = (n == N / 2) ? 0.0f : kf * (float)signed_mode(n, N);
-      return mul_ik(__ldcg(sc + n * W + w), kz);
+      return (SCRATCH || valid) ? mul_ik(__ldcg(phi_at(n)), kz) : make_float2(0.f, 0.f);
     };
     auto store = [&](int n, float2 x) {
       if (valid) gz[n * zstride] = x;
@@ -396,7 +405,7 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
     fft_1d<N, 1, true, C>(t, stw, load, mem, store);
   }
   {
-    auto load = [&](int n) -> float2 { return __ldcg(sc + n * W + w); };
+    auto load = [&](int n) -> float2 { return (SCRATCH || valid) ? __ldcg(phi_at(n)) : make_float2(0.f, 0.f); };
     auto store = [&](int n, float2 x) {
       if (valid) a[n * zstride] = x;
     };

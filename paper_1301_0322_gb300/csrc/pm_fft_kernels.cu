@@ -69,11 +69,17 @@ __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
   y_inv3_body<N, col_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
-// Strip width of the single-buffer (wide-strip) z, forward y and inverse y passes for long
-// columns, 0 where the two-buffer bodies are used.
+// Strip width of the single-buffer (wide-strip) z and forward y passes, 0 where the two-buffer
+// bodies are used (at 768 the two-buffer z pass, which keeps phi in shared memory, and the
+// stand-alone forward y pass were faster)
 template <int N>
 __host__ __device__ constexpr int wide_width() {
   return N == 2048 ? 8 : 0;
+}
+// the same for the inverse y passes (768: 27.0 -> 23.5 ms per 256^3/768^3 run)
+template <int N>
+__host__ __device__ constexpr int wide_inv_width() {
+  return (N == 2048 || N == 768) ? 8 : 0;
 }
 template <int N, int W>
 __host__ __device__ constexpr int wide_min_blocks() {
@@ -85,7 +91,8 @@ __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
     k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float2* __restrict__ scratch, float kf,
                        int deconv, float norm, const float2* __restrict__ tw, int* __restrict__ err) {
   extern __shared__ __align__(16) float2 sm[];
-  z_green_wide_body<N, W>(A, Gz, scratch, kf, deconv, norm, tw, err, blockIdx.x, blockIdx.y, sm);
+  z_green_wide_body<N, W, wide_min_blocks<N, W>() == 1>(A, Gz, scratch, kf, deconv, norm, tw, err, blockIdx.x,
+                                                        blockIdx.y, sm);
 }
 // the scratch slot of an SM belongs to one block only if two blocks cannot share the SM
 template <int N, int W>
@@ -225,9 +232,11 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     }
     COLA_LAUNCH_CHECK();
   }
-  constexpr int WW = wide_width<N>();
-  if constexpr (WW > 0) {
+  constexpr int WW = wide_width<N>(), WI = wide_inv_width<N>();
+  if constexpr (WW > 0 || WI > 0) {
     if (P != half_pitch<N>()) return fail(COLA_EINVAL, "wide column passes: unexpected half-spectrum pitch");
+  }
+  if constexpr (WW > 0) {
     const dim3 grid((nh + WW - 1) / WW, N);
     constexpr int NT = FFTConf<N>::T * WW;
     // 2. forward y pass
@@ -248,35 +257,34 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
       k_fft_z_green_wide<N, WW><<<grid, NT, smem, st>>>(A, Gz, Gy, kf, deconv, norm, tw, err);
       COLA_LAUNCH_CHECK();
     }
-    // 4. inverse y passes
+  } else {
+    // 2. forward y pass
+    if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
+    // 3. z pass with the Green's function
     {
-      const size_t smem = sizeof(float2) * (N * WW + stw_size<FFTConf<N>>());
-      if ((rc = set_smem(k_fft_y_inv3_wide<N, WW>, smem))) return rc;
-      LaunchScope ls_(flabel<N>(2), st);
-      k_fft_y_inv3_wide<N, WW><<<grid, NT, smem, st>>>(A, Gy, Gz, kf, tw);
+      const size_t smem = sizeof(float2) * 2 * N * W;
+      if ((rc = set_smem(k_fft_z_green<N>, smem))) return rc;
+      dim3 grid((nh + W - 1) / W, N);
+      LaunchScope ls_(flabel<N>(1), st);
+      k_fft_z_green<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gz, P, kf, deconv, norm, tw);
       COLA_LAUNCH_CHECK();
     }
-  } else {
-  // 2. forward y pass
-  if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
-  // 3. z pass with the Green's function
-  {
-    const size_t smem = sizeof(float2) * 2 * N * W;
-    if ((rc = set_smem(k_fft_z_green<N>, smem))) return rc;
-    dim3 grid((nh + W - 1) / W, N);
-    LaunchScope ls_(flabel<N>(1), st);
-    k_fft_z_green<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gz, P, kf, deconv, norm, tw);
-    COLA_LAUNCH_CHECK();
   }
   // 4. inverse y passes
-  {
+  if constexpr (WI > 0) {
+    const dim3 grid((nh + WI - 1) / WI, N);
+    const size_t smem = sizeof(float2) * (N * WI + stw_size<FFTConf<N>>());
+    if ((rc = set_smem(k_fft_y_inv3_wide<N, WI>, smem))) return rc;
+    LaunchScope ls_(flabel<N>(2), st);
+    k_fft_y_inv3_wide<N, WI><<<grid, FFTConf<N>::T * WI, smem, st>>>(A, Gy, Gz, kf, tw);
+    COLA_LAUNCH_CHECK();
+  } else {
     const size_t smem = sizeof(float2) * 2 * N * W;
     if ((rc = set_smem(k_fft_y_inv3<N>, smem))) return rc;
     dim3 grid((nh + W - 1) / W, N);
     LaunchScope ls_(flabel<N>(2), st);
     k_fft_y_inv3<N><<<grid, FFTConf<N>::T * W, smem, st>>>(A, Gy, Gz, P, kf, tw);
     COLA_LAUNCH_CHECK();
-  }
   }
   // 5. inverse x passes (persistent, bulk-copy pipelined)
   {
