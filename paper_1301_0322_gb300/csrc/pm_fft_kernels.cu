@@ -76,10 +76,11 @@ template <int N>
 __host__ __device__ constexpr int wide_width() {
   return N == 2048 ? 8 : 0;
 }
-// the same for the inverse y passes (768: 27.0 -> 23.5 ms per 256^3/768^3 run)
+// the same for the inverse y passes (768: 27.0 -> 23.5 ms per 256^3/768^3 run; 16-column strips
+// at 128-256: 1.43 -> 0.75 ms per 128^3/256^3 run)
 template <int N>
 __host__ __device__ constexpr int wide_inv_width() {
-  return (N == 2048 || N == 768) ? 8 : 0;
+  return (N == 2048 || N == 768) ? 8 : ((N >= 128 && N <= 256) ? 16 : 0);
 }
 template <int N, int W>
 __host__ __device__ constexpr int wide_min_blocks() {
