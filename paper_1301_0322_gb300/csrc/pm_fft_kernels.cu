@@ -71,10 +71,11 @@ __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
 
 // Strip width of the single-buffer (wide-strip) z and forward y passes, 0 where the two-buffer
 // bodies are used (at 768 the two-buffer z pass, which keeps phi in shared memory, and the
-// stand-alone forward y pass were faster)
+// stand-alone forward y pass were faster; at 256, 16-column strips: z 0.88 -> 0.75, forward y
+// 0.34 -> 0.31 ms per 128^3/256^3 run)
 template <int N>
 __host__ __device__ constexpr int wide_width() {
-  return N == 2048 ? 8 : 0;
+  return N == 2048 ? 8 : ((N >= 128 && N <= 256) ? 16 : 0);
 }
 // the same for the inverse y passes (768: 27.0 -> 23.5 ms per 256^3/768^3 run; 16-column strips
 // at 128-256: 1.43 -> 0.75 ms per 128^3/256^3 run)
