@@ -448,7 +448,7 @@ int cola_status(cola_plan* plan, cola_stream stream) {
   if (err & kErrTimeout) return fail(COLA_ETIMEOUT, "a kernel gave up waiting for its bulk copies");
   if (err & kErrUnion) return fail(COLA_ETIMEOUT, "friends-of-friends: union-find retries ran out");
   if (err & kErrSmIds)
-    return fail(COLA_EUNSUPPORTED, "the device numbers more SMs than the 2048-point z pass has scratch slots");
+    return fail(COLA_EUNSUPPORTED, "the wide z pass found no scratch slot for its SM (more SM ids than slots)");
   if (err & kErrNonFinite) return fail(COLA_EOVERFLOW, "non-finite particle displacement");
   if (err & kErrOverflow) return fail(COLA_EOVERFLOW, "fixed-point density overflow (too many particles per cell)");
   return COLA_OK;

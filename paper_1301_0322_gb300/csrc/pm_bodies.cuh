@@ -320,21 +320,26 @@ __host__ __device__ constexpr int wide_z_table_offset() {
 // scratch slots of the wide z pass (one per SM id, N W float2 each)
 constexpr int kZScratchSlots = 512;
 
-// z pass with the Green's function, one exchange buffer.  SCRATCH (one block per SM): the
-// forward transform of the strip (Green's function applied as it is stored) goes to a scratch
-// slot of this SM, contiguous [n][w]; the inverse transforms of i k_z phi (-> Gz) and of phi
-// (-> A) read it back from L2 as whole 128-byte lines (the strip itself spans N rows 16.8 MB
-// apart at N = 2048).  One block fits per SM (shared memory), so the slot of %smid is this
-// block's alone while it runs.  Without SCRATCH (two blocks per SM) phi goes to A and the
-// inverse transforms read it back from there (an L2 hit).
-// block (bx, ky): W columns kx of the slab ky (T(N) W threads); scratch: kZScratchSlots N W float2
-template <int N, int W, bool SCRATCH, class C = FFTConf<N>>
+// z pass with the Green's function, one exchange buffer.  With KS > 0 scratch slots per SM the
+// forward transform of the strip (Green's function applied as it is stored) goes to a slot of
+// this SM, contiguous [n][w], and the inverse transforms of i k_z phi (-> Gz) and of phi (-> A)
+// read it back from L2 as whole 128-byte lines (the strip itself spans N rows N (N/2+1) 8 bytes
+// apart: 16.8 MB at N = 2048).  KS = 1: one block fits per SM (shared memory), so the slot of
+// %smid is the block's own while it runs; KS > 1: a block claims one of its SM's KS slots
+// (compare-and-swap on busy[], a bounded number of rounds) and frees it when it is done, KS
+// being above the blocks that fit on an SM.  KS = 0: phi goes to A and the inverse transforms
+// read it back from there (an L2 hit).
+// block (bx, ky): W columns kx of the slab ky (T(N) W threads); scratch: kZScratchSlots KS N W
+// float2; busy: kZScratchSlots KS ints, zero between launches
+template <int N, int W, int KS, class C = FFTConf<N>>
 __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2* __restrict__ Gz,
-                                                  float2* __restrict__ scratch, float kf, int deconv, float norm,
-                                                  const float2* __restrict__ tw, int* __restrict__ err, int bx,
-                                                  int ky, float2* sm) {
+                                                  float2* __restrict__ scratch, int* __restrict__ busy, float kf,
+                                                  int deconv, float norm, const float2* __restrict__ tw,
+                                                  int* __restrict__ err, int bx, int ky, float2* sm) {
   constexpr int nh = N / 2 + 1, NT = C::T * W, P = half_pitch<N>();
+  constexpr bool SCRATCH = KS > 0;
   float2* sc = nullptr;
+  int* my_flag = nullptr;
   if constexpr (SCRATCH) {
     unsigned smid, nsmid;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
@@ -343,7 +348,25 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
       if (threadIdx.x == 0) atomicOr(err, kErrSmIds);
       return;
     }
-    sc = scratch + (int64_t)smid * (N * W);
+    int slot = (int)smid * KS;
+    if constexpr (KS > 1) {
+      __shared__ int claimed;
+      if (threadIdx.x == 0) {
+        int got = -1;
+        for (int round = 0; round < 1024 && got < 0; ++round)
+          for (int k = 0; k < KS && got < 0; ++k)
+            if (atomicCAS(busy + slot + k, 0, 1) == 0) got = k;
+        claimed = got;
+      }
+      __syncthreads();
+      if (claimed < 0) {
+        if (threadIdx.x == 0) atomicOr(err, kErrSmIds);
+        return;
+      }
+      slot += claimed;
+      my_flag = busy + slot;
+    }
+    sc = scratch + (int64_t)slot * (N * W);
   }
   float2* S = sm;
   float* sz2 = reinterpret_cast<float*>(sm + N * W);
@@ -410,6 +433,10 @@ __device__ __forceinline__ void z_green_wide_body(float2* __restrict__ A, float2
       if (valid) a[n * zstride] = x;
     };
     fft_1d<N, 1, true, C>(t, stw, load, mem, store);
+  }
+  if constexpr (KS > 1) {
+    __syncthreads();  // every read of the slot is done: free it (the exchange returns when done)
+    if (threadIdx.x == 0) atomicExch(my_flag, 0);
   }
 }
 

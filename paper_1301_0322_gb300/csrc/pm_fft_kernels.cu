@@ -69,13 +69,17 @@ __global__ void __launch_bounds__(FFTConf<N>::T * col_width<N>(), 2)
   y_inv3_body<N, col_width<N>()>(B, Gy, Gz, P, kf, tw, blockIdx.x, blockIdx.y, sm);
 }
 
-// Strip width of the single-buffer (wide-strip) z and forward y passes, 0 where the two-buffer
-// bodies are used (at 768 the two-buffer z pass, which keeps phi in shared memory, and the
-// stand-alone forward y pass were faster; at 256, 16-column strips: z 0.88 -> 0.75, forward y
-// 0.34 -> 0.31 ms per 128^3/256^3 run)
+// Strip widths of the single-buffer (wide-strip) z, forward y and inverse y passes, 0 where the
+// two-buffer bodies (z, inverse y) or the stand-alone column pass (forward y) are used.  At 256,
+// 16-column strips: z 0.88 -> 0.75, forward y 0.34 -> 0.31 ms per 128^3/256^3 run; at 768 the
+// stand-alone forward y pass stays faster.
 template <int N>
 __host__ __device__ constexpr int wide_width() {
-  return N == 2048 ? 8 : ((N >= 128 && N <= 256) ? 16 : 0);
+  return (N == 2048 || N == 768) ? 8 : ((N >= 128 && N <= 256) ? 16 : 0);
+}
+template <int N>
+__host__ __device__ constexpr int wide_fwd_width() {
+  return N == 768 ? 0 : wide_width<N>();
 }
 // the same for the inverse y passes (768: 27.0 -> 23.5 ms per 256^3/768^3 run; 16-column strips
 // at 128-256: 1.43 -> 0.75 ms per 128^3/256^3 run)
@@ -88,13 +92,22 @@ __host__ __device__ constexpr int wide_min_blocks() {
   return FFTConf<N>::T * W >= 1024 ? 1 : 2;
 }
 
+// scratch slots per SM of the wide z pass: the SM's own slot where one block fits (2048), four
+// claimed slots at 768 (at most three blocks of 58 KB fit), none elsewhere
+template <int N, int W>
+__host__ __device__ constexpr int wide_z_slots() {
+  return wide_min_blocks<N, W>() == 1 ? 1 : (N == 768 ? 4 : 0);
+}
+// slot flags of the claimed scratch slots (zero between launches: every block frees its slot)
+__device__ int g_zslot_busy[kZScratchSlots * 4];
+
 template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
     k_fft_z_green_wide(float2* __restrict__ A, float2* __restrict__ Gz, float2* __restrict__ scratch, float kf,
                        int deconv, float norm, const float2* __restrict__ tw, int* __restrict__ err) {
   extern __shared__ __align__(16) float2 sm[];
-  z_green_wide_body<N, W, wide_min_blocks<N, W>() == 1>(A, Gz, scratch, kf, deconv, norm, tw, err, blockIdx.x,
-                                                        blockIdx.y, sm);
+  z_green_wide_body<N, W, wide_z_slots<N, W>()>(A, Gz, scratch, g_zslot_busy, kf, deconv, norm, tw, err,
+                                                 blockIdx.x, blockIdx.y, sm);
 }
 // the scratch slot of an SM belongs to one block only if two blocks cannot share the SM
 template <int N, int W>
@@ -102,6 +115,7 @@ constexpr size_t wide_z_smem() {
   return sizeof(float2) * (wide_z_table_offset<N, W>() + stw_size<FFTConf<N>>());
 }
 static_assert(2 * wide_z_smem<2048, 8>() > 228 * 1024, "two wide z blocks would fit on one SM");
+static_assert(4 * (wide_z_smem<768, 8>() + 1024) > 228 * 1024, "four wide z blocks would fit on one SM");
 
 template <int N, int W>
 __global__ void __launch_bounds__(FFTConf<N>::T * W, wide_min_blocks<N, W>())
@@ -238,21 +252,26 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
   if constexpr (WW > 0 || WI > 0) {
     if (P != half_pitch<N>()) return fail(COLA_EINVAL, "wide column passes: unexpected half-spectrum pitch");
   }
+  // 2. forward y pass
+  constexpr int WF = wide_fwd_width<N>();
+  if constexpr (WF > 0) {
+    const dim3 grid((nh + WF - 1) / WF, N);
+    const size_t smem = sizeof(float2) * (N * WF + stw_size<FFTConf<N>>());
+    if ((rc = set_smem(k_fft_y_fwd_wide<N, WF>, smem))) return rc;
+    LaunchScope ls_(flabel<N>(4), st);
+    k_fft_y_fwd_wide<N, WF><<<grid, FFTConf<N>::T * WF, smem, st>>>(A, tw);
+    COLA_LAUNCH_CHECK();
+  } else {
+    if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
+  }
   if constexpr (WW > 0) {
     const dim3 grid((nh + WW - 1) / WW, N);
     constexpr int NT = FFTConf<N>::T * WW;
-    // 2. forward y pass
-    {
-      const size_t smem = sizeof(float2) * (N * WW + stw_size<FFTConf<N>>());
-      if ((rc = set_smem(k_fft_y_fwd_wide<N, WW>, smem))) return rc;
-      LaunchScope ls_(flabel<N>(4), st);
-      k_fft_y_fwd_wide<N, WW><<<grid, NT, smem, st>>>(A, tw);
-      COLA_LAUNCH_CHECK();
-    }
     // 3. z pass with the Green's function; its scratch slots sit at the start of Gy, which the
     // inverse y passes write only afterwards
     {
-      static_assert((int64_t)kZScratchSlots * N * WW <= (int64_t)N * N * half_pitch<N>(), "scratch exceeds Gy");
+      static_assert((int64_t)kZScratchSlots * wide_z_slots<N, WW>() * N * WW <= (int64_t)N * N * half_pitch<N>(),
+                    "scratch exceeds Gy");
       const size_t smem = wide_z_smem<N, WW>();
       if ((rc = set_smem(k_fft_z_green_wide<N, WW>, smem))) return rc;
       LaunchScope ls_(flabel<N>(1), st);
@@ -260,8 +279,6 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
       COLA_LAUNCH_CHECK();
     }
   } else {
-    // 2. forward y pass
-    if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
     // 3. z pass with the Green's function
     {
       const size_t smem = sizeof(float2) * 2 * N * W;
