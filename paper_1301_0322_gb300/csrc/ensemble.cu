@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_deposit(const BoxDesc* __rest
   }
 }
 
-// column passes: kind 0 = forward y, 1 = z with the Green's function, 2 = inverse y (three outputs)
+// column passes: kind 0 = forward y, 1 = z with the Green's function, 2 = inverse y (three
+// outputs); single-buffer strips of W = NT / T(N) columns, stage twiddles from shared memory
+// (the bodies of the single-box passes at 128-256; the z pass keeps phi in A)
 template <int NT, int KIND, int V>
 __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restrict__ boxes, const int* __restrict__ starts,
                                               int nbox) {
@@ -195,12 +197,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) ke_cols(const BoxDesc* __restric
     using C = FFTConfV<N, V>;                                                                             \
     constexpr int W = NT / C::T, nbx = (N / 2 + 1 + W - 1) / W;                                           \
     const int bx = local % nbx, slab = local / nbx;                                                       \
-    if (KIND == 0)                                                                                        \
-      cols_body<N, W, false, C>(d.A, (int64_t)N * d.P, d.P, N / 2 + 1, d.tw, bx, slab, sm);              \
-    else if (KIND == 1)                                                                                   \
-      z_green_body<N, W, C>(d.A, d.Gz, d.P, d.kf, d.deconv, d.norm, d.tw, bx, slab, sm);                  \
-    else                                                                                                  \
-      y_inv3_body<N, W, C>(d.A, d.Gy, d.Gz, d.P, d.kf, d.tw, bx, slab, sm);                               \
+    if (KIND == 0) {                                                                                      \
+      float2* stab = sm + N * W;                                                                          \
+      stw_fill<C, 1>(stab, d.tw, threadIdx.x, NT);                                                        \
+      cols_body<N, W, false, C>(d.A, (int64_t)N * d.P, d.P, N / 2 + 1, SmemTw<C>{stab}, bx, slab, sm);    \
+    } else if (KIND == 1) {                                                                               \
+      z_green_wide_body<N, W, 0, C>(d.A, d.Gz, nullptr, nullptr, d.kf, d.deconv, d.norm, d.tw, d.err, bx, \
+                                    slab, sm);                                                            \
+    } else {                                                                                              \
+      y_inv3_wide_body<N, W, C>(d.A, d.Gy, d.Gz, d.kf, d.tw, bx, slab, sm);                               \
+    }                                                                                                     \
   } break;
       COLA_ENS_SIZES(X)
 #undef X
@@ -532,6 +538,19 @@ int kernel_attrs(cola_ensemble* e) {
   return COLA_OK;
 }
 
+// stage twiddle table of an n-point column transform in radix variant v (float2 entries)
+int ens_stw_size(int n, int v) {
+  switch (n) {
+#define X(N) \
+  case N:    \
+    return v ? stw_size<FFTConfV<N, 1>>() : stw_size<FFTConfV<N, 0>>();
+    COLA_ENS_SIZES(X)
+#undef X
+    default:
+      return 0;
+  }
+}
+
 // inverse-x stage twiddle tables of every ensemble size (float2 entries)
 int ens_c2r_tab_total(int v) {
   return v ? ens_c2r_tab_offset<1>(0) : ens_c2r_tab_offset<0>(0);
@@ -588,14 +607,14 @@ int configure(cola_ensemble* e, cudaStream_t st) {
     for (int l = 0; l < kENumLists; ++l) items[(size_t)b * kENumLists + l] = it[l];
     const int M = n / 2;
     const size_t dep = sizeof(unsigned long long) * sh.rows * std::max(n, xrow_ld_host(M));
-    const size_t cols = sizeof(float2) * n * sh.W;
+    const size_t cols = sizeof(float2) * (n * sh.W + ens_stw_size(n, e->tuning.radix));
     d.c2r_rb = sh.RB;
     d.c2r_ld = xrow_ld_host(M);
     c2r_buf = std::max(c2r_buf, (size_t)sh.RB * xrow_ld_host(M));
     e->smem[kKDeposit] = std::max(e->smem[kKDeposit], dep);
     e->smem[kKYfwd] = std::max(e->smem[kKYfwd], cols);
-    e->smem[kKZgreen] = std::max(e->smem[kKZgreen], 2 * cols);
-    e->smem[kKYinv] = std::max(e->smem[kKYinv], 2 * cols);
+    e->smem[kKZgreen] = std::max(e->smem[kKZgreen], cols + sizeof(float2) * ((n + sh.W + 3) / 4 * 2));
+    e->smem[kKYinv] = std::max(e->smem[kKYinv], cols);
   }
   if (bins > e->max_bins_total) return fail(COLA_EINVAL, "ensemble: bin count above the workspace sizing");
   e->total_bins = bins;
