@@ -185,9 +185,10 @@ int cola_power(cola_plan* plan, const float* delta, int32_t nbins, double* k, do
                int64_t* nmodes, cola_stream stream);
 
 /* The power spectrum of cola_power of the CIC density of cola_density at displacements s (Sec.
- * 3.1), without a caller-owned mesh: the density and its transform go to the plan's force
+ * 3.1), without a caller-owned mesh: the transform of the density goes to the plan's force
  * meshes, which hold nothing between calls that write them (the next force evaluation rebuilds
- * them).  The same kernels as cola_density + cola_power, so the same k, pk, nmodes bit for bit.
+ * them), through the force evaluation's fused deposit and real-to-complex pass.  The same
+ * arithmetic as cola_density + cola_power, so the same k, pk, nmodes bit for bit.
  * s: device float32 [3][np^3] (read only); k, pk: device float64 [nbins]; nmodes: device int64
  * [nbins]; nbins <= ng. */
 int cola_density_power(cola_plan* plan, const float* s, int32_t nbins, double* k, double* pk, int64_t* nmodes,

@@ -396,10 +396,9 @@ int cola_density_power(cola_plan* plan, const float* s, int32_t nbins, double* k
   if (nbins < 1 || nbins > plan->geo.ng) return fail(COLA_EINVAL, "nbins must be in [1, ng]");
   cudaStream_t st = (cudaStream_t)stream;
   Workspace& w = plan->ws;
-  float* delta = w.freal;  // ng^3 floats of the first force mesh
   if ((rc = bin_particles(plan, s, st))) return rc;
-  if ((rc = launch_deposit(plan->geo, plan->tiles, w.rec, w.offsets, nullptr, delta, w.err, st))) return rc;
-  if ((rc = fft3d_r2c(plan->geo.ng, plan->Pg, delta, w.meshA, w.tw_g, st))) return rc;
+  if ((rc = launch_density_spectrum(plan->geo, plan->tiles, w.rec, w.offsets, w.meshA, plan->Pg, w.tw_g, w.err, st)))
+    return rc;
   if ((rc = launch_power_bin(plan->geo.ng, plan->Pg, plan->cfg.box, nbins, w.meshA, w.pk_partial, st))) return rc;
   return launch_power_finish(nbins, w.pk_partial, k, pk, nmodes, st);
 }

@@ -176,6 +176,10 @@ int launch_kspace_force(int ng, int P, double box, int deconv, const float2* dk,
                         cudaStream_t st);
 // the fused mesh passes of one force evaluation (pm_fft_kernels.cu): deposit + x r2c, y pass,
 // z pass with the Green's function, inverse y passes, inverse x passes -> F [3][ng^3]
+// the half spectrum A of the density of the binned particles: the force evaluation's fused
+// deposit + x r2c, then the forward y and z passes (no Green's function)
+int launch_density_spectrum(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets, float2* A,
+                            int P, const float2* tw, int* err, cudaStream_t st);
 int launch_force_passes(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                         float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv, const float2* tw,
                         int* err, cudaStream_t st);

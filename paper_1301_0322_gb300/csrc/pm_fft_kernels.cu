@@ -219,6 +219,52 @@ static const char* flabel(int kind) {
   return names[kind].c_str();
 }
 
+// 1. deposit + x r2c of every tile into the half spectrum A
+template <int N>
+static int deposit_fftx_t(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets, float2* A, int P,
+                          const float2* tw, int* err, cudaStream_t st) {
+  constexpr int M = N / 2;
+  int rc;
+  const double n3 = (double)N * N * N;
+  const float dscale = (float)(n3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
+  if (tl.ty == 4 && tl.tz == 2) {
+    const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 4, 2>() + deposit_table_size<N>());
+    if ((rc = set_smem(k_deposit_fftx<N, 4, 2>, smem))) return rc;
+    LaunchScope ls_(flabel<N>(0), st);
+    k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, rec, offsets, A, P, tw,
+                                                                                dscale, err);
+  } else if (tl.ty == 2 && tl.tz == 2) {
+    const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 2, 2>() + deposit_table_size<N>());
+    if ((rc = set_smem(k_deposit_fftx<N, 2, 2>, smem))) return rc;
+    LaunchScope ls_(flabel<N>(0), st);
+    k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, rec, offsets, A, P, tw,
+                                                                                dscale, err);
+  } else {
+    return fail(COLA_EUNSUPPORTED, "fused deposit: unsupported tile shape");
+  }
+  COLA_LAUNCH_CHECK();
+  return COLA_OK;
+}
+
+// 2. forward y pass of the half spectrum A
+template <int N>
+static int forward_y_t(float2* A, int P, const float2* tw, cudaStream_t st) {
+  constexpr int nh = N / 2 + 1, WF = wide_fwd_width<N>();
+  if constexpr (WF > 0) {
+    if (P != half_pitch<N>()) return fail(COLA_EINVAL, "wide column passes: unexpected half-spectrum pitch");
+    int rc;
+    const dim3 grid((nh + WF - 1) / WF, N);
+    const size_t smem = sizeof(float2) * (N * WF + stw_size<FFTConf<N>>());
+    if ((rc = set_smem(k_fft_y_fwd_wide<N, WF>, smem))) return rc;
+    LaunchScope ls_(flabel<N>(4), st);
+    k_fft_y_fwd_wide<N, WF><<<grid, FFTConf<N>::T * WF, smem, st>>>(A, tw);
+    COLA_LAUNCH_CHECK();
+    return COLA_OK;
+  } else {
+    return launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st);
+  }
+}
+
 template <int N>
 static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
                           float2* A, float2* Gy, float2* Gz, float* F, int P, double box, int deconv,
@@ -227,43 +273,12 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const float norm = (float)(1.0 / ((double)N * N * N));
   int rc;
-  // 1. deposit + x r2c
-  {
-    const double n3 = (double)N * N * N;
-    const float dscale = (float)(n3 / ((double)g.np3 * std::ldexp(1.0, 3 * g.fbits)));
-    if (tl.ty == 4 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 4, 2>() + deposit_table_size<N>());
-      if ((rc = set_smem(k_deposit_fftx<N, 4, 2>, smem))) return rc;
-      LaunchScope ls_(flabel<N>(0), st);
-      k_deposit_fftx<N, 4, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 8, smem, st>>>(g, tl, rec, offsets, A, P, tw,
-                                                                                  dscale, err);
-    } else if (tl.ty == 2 && tl.tz == 2) {
-      const size_t smem = sizeof(unsigned long long) * (deposit_acc_cells<N, 2, 2>() + deposit_table_size<N>());
-      if ((rc = set_smem(k_deposit_fftx<N, 2, 2>, smem))) return rc;
-      LaunchScope ls_(flabel<N>(0), st);
-      k_deposit_fftx<N, 2, 2><<<tl.nty * tl.ntz, FFTConf<M>::T * 4, smem, st>>>(g, tl, rec, offsets, A, P, tw,
-                                                                                  dscale, err);
-    } else {
-      return fail(COLA_EUNSUPPORTED, "fused deposit: unsupported tile shape");
-    }
-    COLA_LAUNCH_CHECK();
-  }
+  if ((rc = deposit_fftx_t<N>(g, tl, rec, offsets, A, P, tw, err, st))) return rc;
   constexpr int WW = wide_width<N>(), WI = wide_inv_width<N>();
   if constexpr (WW > 0 || WI > 0) {
     if (P != half_pitch<N>()) return fail(COLA_EINVAL, "wide column passes: unexpected half-spectrum pitch");
   }
-  // 2. forward y pass
-  constexpr int WF = wide_fwd_width<N>();
-  if constexpr (WF > 0) {
-    const dim3 grid((nh + WF - 1) / WF, N);
-    const size_t smem = sizeof(float2) * (N * WF + stw_size<FFTConf<N>>());
-    if ((rc = set_smem(k_fft_y_fwd_wide<N, WF>, smem))) return rc;
-    LaunchScope ls_(flabel<N>(4), st);
-    k_fft_y_fwd_wide<N, WF><<<grid, FFTConf<N>::T * WF, smem, st>>>(A, tw);
-    COLA_LAUNCH_CHECK();
-  } else {
-    if ((rc = launch_fft_cols(N, false, A, N, (int64_t)N * P, P, nh, tw, st))) return rc;
-  }
+  if ((rc = forward_y_t<N>(A, P, tw, st))) return rc;
   if constexpr (WW > 0) {
     const dim3 grid((nh + WW - 1) / WW, N);
     constexpr int NT = FFTConf<N>::T * WW;
@@ -332,6 +347,23 @@ static int force_passes_t(const Geometry& g, const Tiles& tl, const uint4* rec, 
     COLA_LAUNCH_CHECK();
   }
   return COLA_OK;
+}
+
+int launch_density_spectrum(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets, float2* A,
+                            int P, const float2* tw, int* err, cudaStream_t st) {
+  switch (g.ng) {
+#define X(N)                                                                                          \
+  case N: {                                                                                           \
+    int rc;                                                                                           \
+    if ((rc = deposit_fftx_t<N>(g, tl, rec, offsets, A, P, tw, err, st))) return rc;                  \
+    if ((rc = forward_y_t<N>(A, P, tw, st))) return rc;                                               \
+    return launch_fft_cols(N, false, A, N, P, (int64_t)N * P, N / 2 + 1, tw, st); /* z: slab = y */ \
+  }
+    X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048)
+#undef X
+    default:
+      return fail(COLA_EUNSUPPORTED, "density spectrum: unsupported mesh size");
+  }
 }
 
 int launch_force_passes(const Geometry& g, const Tiles& tl, const uint4* rec, const int* offsets,
