@@ -448,6 +448,8 @@ def measure_workload(args, workload, dev, rank, world, with_fof):
         kv["share"] = kv["ms"] / total_ms
         alg = algorithmic_bytes(name, n_p, ng)
         kv["avg_launch_ms"] = kv["ms"] / kv["launches"]
+        if alg and name in ("power_bin", "cross_bin"):
+            alg /= kv["launches"] / args.steps  # one spectrum read, over the shell-range launches of a P(k)
         if alg:
             kv["bytes_per_launch"] = alg
             kv["achieved_gbs"] = alg / (kv["avg_launch_ms"] * 1e-3) / 1e9

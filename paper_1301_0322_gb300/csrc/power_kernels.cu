@@ -29,40 +29,52 @@ __device__ __forceinline__ float sinc_pi_p(int n, int ng) {
 // fixed order and the finish kernel adds the blocks in block order: the result is
 // deterministic.  NF = 1: one field, partial layout [block][shell][3] = (sum w |k|, sum w P,
 // sum w); NF = 2: two fields a, b, [block][shell][5] = (sum w |k|, sum w P_a, sum w P_b,
-// sum w P_ab, sum w) with P_ab from Re(a b^*).
+// sum w P_ab, sum w) with P_ab from Re(a b^*).  One launch bins the shells b0 .. b1 - 1 of the
+// nbins (the accumulators of a range of shells per warp leave room for more warps than those of
+// all shells); chunks of modes outside the range are skipped.
 template <int NF>
-__global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, const float2* __restrict__ dk,
-                            const float2* __restrict__ dk2, double* __restrict__ partial) {
+__global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, int b0, int b1,
+                            const float2* __restrict__ dk, const float2* __restrict__ dk2,
+                            double* __restrict__ partial) {
   constexpr int NQ = NF == 1 ? 3 : 5;
   static_assert(NQ <= kPowerQuantities, "partial sums beyond the sized buffers");
   extern __shared__ double pacc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nh = ng / 2 + 1;
   // 1 / W_x^2 = sinc^-4 of every k_x, once per block (after the accumulators)
-  float* inv_wx2 = reinterpret_cast<float*>(pacc + (size_t)nwarps * nbins * NQ);
-  for (int i = threadIdx.x; i < nwarps * nbins * NQ; i += blockDim.x) pacc[i] = 0.0;
+  const int nb = b1 - b0;
+  float* inv_wx2 = reinterpret_cast<float*>(pacc + (size_t)nwarps * nb * NQ);
+  for (int i = threadIdx.x; i < nwarps * nb * NQ; i += blockDim.x) pacc[i] = 0.0;
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     const float sx = sinc_pi_p(i, ng), wx = sx * sx;
     inv_wx2[i] = 1.0f / (wx * wx);
   }
   __syncthreads();
-  double* mine = pacc + (size_t)warp * nbins * NQ;
+  double* mine = pacc + (size_t)warp * nb * NQ;
+  // the shells of the range hold the modes with lo_m < |n|^2 <= hi_m
+  const int lo_m = b0 * (b0 + 1), hi_m = b1 * (b1 + 1);
   const int64_t nrows = (int64_t)ng * ng;
   for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < nrows; row += (int64_t)gridDim.x * nwarps) {
     const int ky = (int)(row % ng), kz = (int)(row / ng);
     const int ny = ky < ng / 2 ? ky : ky - ng, nz = kz < ng / 2 ? kz : kz - ng;
     const int myz = ny * ny + nz * nz;
-    // shell b <= nbins iff |n|^2 <= nbins (nbins + 1): rows and chunks beyond that hold no mode
-    // of the requested shells and are skipped (warp-uniform)
-    const int lim = nbins * (nbins + 1) - myz;
+    // rows and chunks with no mode of the range's shells are skipped (warp-uniform)
+    const int lim = hi_m - myz;
     if (lim < 0) continue;
+    // the first chunk group with a mode above lo_m: c^2 > lo_m - myz for some c in the group
+    int gstart = 0;
+    if (lo_m - myz > 0) {
+      int c = (int)sqrtf((float)(lo_m - myz));
+      while (c > 0 && c * c > lo_m - myz) --c;
+      gstart = (c / (32 * kPowerChunks)) * (32 * kPowerChunks);
+    }
     const float sy = sinc_pi_p(ny, ng), sz = sinc_pi_p(nz, ng);
     const float wyz = (sy * sy) * (sz * sz);
     const float row_scale = pnorm / (wyz * wyz);
     const float2* rowp = dk + row * P;
     const float2* rowq = NF == 2 ? dk2 + row * P : nullptr;
     // chunks of 32 k_x in groups of kPowerChunks whose loads are all issued first
-    for (int g0 = 0; g0 < nh && g0 * g0 <= lim; g0 += 32 * kPowerChunks) {
+    for (int g0 = gstart; g0 < nh && g0 * g0 <= lim; g0 += 32 * kPowerChunks) {
       float2 dv[kPowerChunks], ev[kPowerChunks];
 #pragma unroll
       for (int u = 0; u < kPowerChunks; ++u) {
@@ -82,8 +94,8 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
         if (kx < nh) {
           const int m = kx * kx + myz;
           const int sb = shell_of(m);
-          if (sb >= 1 && sb <= nbins) {
-            b = sb - 1;
+          if (sb - 1 >= b0 && sb - 1 < b1) {
+            b = sb - 1 - b0;
             const float w = (kx == 0 || kx == ng / 2) ? 1.f : 2.f;
             const float2 d = dv[u];
             const float scale = w * (row_scale * inv_wx2[kx]);  // w P-normalisation / W(k)^2
@@ -119,10 +131,10 @@ __global__ void k_power_bin(int ng, int P, float kf, float pnorm, int nbins, con
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nbins * NQ; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nb * NQ; i += blockDim.x) {
     double t = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) t += pacc[(size_t)wv * nbins * NQ + i];
-    partial[(size_t)blockIdx.x * nbins * NQ + i] = t;
+    for (int wv = 0; wv < nwarps; ++wv) t += pacc[(size_t)wv * nb * NQ + i];
+    partial[((size_t)blockIdx.x * nbins + b0) * NQ + i] = t;
   }
 }
 
@@ -176,9 +188,16 @@ __global__ void k_unpad(int n, int P, const float2* __restrict__ in, float2* __r
   }
 }
 
-static int power_warps(int nbins, int nq) {
-  const int w = (int)((160 * 1024) / ((size_t)nbins * nq * sizeof(double)));
-  return std::max(1, std::min(8, w));
+// 8 warps per block: the shells in one launch if their per-warp float64 accumulators still let
+// two blocks share an SM (at most 110 KB a block), else in equal ranges whose accumulators let
+// three (at most 64 KB)
+constexpr int kPowerWarps = 8;
+static int power_range(int nbins, int nq) {
+  const size_t per_shell = (size_t)kPowerWarps * nq * sizeof(double);
+  const int two = (int)((110 * 1024) / per_shell), three = (int)((64 * 1024) / per_shell);
+  if (nbins <= two) return nbins;
+  const int launches = (nbins + three - 1) / three;
+  return (nbins + launches - 1) / launches;
 }
 
 int power_partial_doubles(int nbins) { return kPowerBlocks * nbins * kPowerQuantities; }
@@ -191,16 +210,20 @@ static int power_bin_t(int ng, int P, double box, int nbins, const float2* dk, c
   const float kf = (float)(2.0 * 3.14159265358979323846 / box);
   const double ng6 = std::pow((double)ng, 6.0);
   const float pnorm = (float)(box * box * box / ng6);
-  const int warps = power_warps(nbins, NQ);
-  const size_t smem = (size_t)warps * nbins * NQ * sizeof(double) + sizeof(float) * (ng / 2 + 1);
-  if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "power spectrum: too many bins for shared memory");
+  const int range = power_range(nbins, NQ);
+  const size_t smem = (size_t)kPowerWarps * range * NQ * sizeof(double) + sizeof(float) * (ng / 2 + 1);
+  if (smem > 227 * 1024) return fail(COLA_EUNSUPPORTED, "power spectrum: mesh too large for shared memory");
   if (smem > 32 * 1024)
     COLA_CUDA_CHECK(cudaFuncSetAttribute(k_power_bin<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  {
-    LaunchScope ls_(NF == 1 ? "power_bin" : "cross_bin", st);
-    k_power_bin<NF><<<kPowerBlocks, 32 * warps, smem, st>>>(ng, P, kf, pnorm, nbins, dk, dk2, partial);
+  for (int b0 = 0; b0 < nbins; b0 += range) {
+    const int b1 = std::min(nbins, b0 + range);
+    {
+      LaunchScope ls_(NF == 1 ? "power_bin" : "cross_bin", st);
+      k_power_bin<NF><<<kPowerBlocks, 32 * kPowerWarps, smem, st>>>(ng, P, kf, pnorm, nbins, b0, b1, dk, dk2,
+                                                                      partial);
+    }
+    COLA_LAUNCH_CHECK();
   }
-  COLA_LAUNCH_CHECK();
   return COLA_OK;
 }
 

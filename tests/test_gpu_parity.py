@@ -142,13 +142,13 @@ def test_ic_2lpt_matches_oracle(cola, n_p, box):
     assert np.all(v == 0.0)
 
 
-@pytest.mark.parametrize("ng", [64, 96])
-def test_power_matches_oracle(cola, ng):
+@pytest.mark.parametrize("ng,nbins", [(64, 32), (96, 48), (384, 384)])
+def test_power_matches_oracle(cola, ng, nbins):
     box = 100.0
     plan = cola.Plan(np_side=32, ng=ng, box=box)
     d = inputs.gaussian_noise(ng, 31) * 0.3
-    k, p, nm = (host(t) for t in plan.power(dev(d), ng // 2))
-    kr, pr, nr = opower.power_spectrum(d.reshape(ng, ng, ng).astype(np.float64), box, ng // 2)
+    k, p, nm = (host(t) for t in plan.power(dev(d), nbins))
+    kr, pr, nr = opower.power_spectrum(d.reshape(ng, ng, ng).astype(np.float64), box, nbins)
     assert np.array_equal(nm, nr)
     assert np.allclose(k, kr, rtol=1e-6)
     assert np.allclose(p, pr, rtol=1e-5)
@@ -213,6 +213,27 @@ def test_nonfinite_positions_are_reported(cola):
         plan.status()
     assert e.value.code == 3
     plan.status()  # the error was cleared
+
+
+def test_cross_power_in_shell_ranges_matches_oracle(cola):
+    # 384 shells of five sums each are more than one binning launch takes (352): binned in two
+    # ranges of 192; two correlated fields, so that P_ab stays away from zero
+    ng, box, nb = 384, 100.0, 384
+    plan = cola.Plan(np_side=32, ng=ng, box=box)
+    da = inputs.gaussian_noise(ng, 41) * 0.3
+    db = da + 0.5 * inputs.gaussian_noise(ng, 42) * 0.3
+    got = [host(t) for t in plan.cross_power(dev(da), dev(db), nb)]
+    plan.status()
+    ref = opower.cross_correlation(da.reshape(ng, ng, ng).astype(np.float64),
+                                   db.reshape(ng, ng, ng).astype(np.float64), box, nb)
+    k, pa, pb, pab, rho, nmax, nm = got
+    assert np.array_equal(nm, ref[6])
+    full = ref[6] > 0  # shells beyond |n| = sqrt(3) ng/2 hold no mode
+    assert full.sum() > 300 and np.all(pa[~full] == 0.0)
+    assert np.allclose(k, ref[0], rtol=1e-6)
+    for g_, r_ in ((pa, ref[1]), (pb, ref[2]), (pab, ref[3])):
+        assert np.abs(g_[full] / r_[full] - 1.0).max() <= 1e-4
+    assert np.abs(rho[full] - ref[4][full]).max() <= 1e-5
 
 
 def test_cross_power_matches_oracle(cola):
