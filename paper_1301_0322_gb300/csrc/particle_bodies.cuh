@@ -1,7 +1,8 @@
 // Per-particle device bodies of a COLA force evaluation (Sec. 2 PM code; App. A.3 eq. KDKALC),
-// shared by the single-box kernels and the multi-box (ensemble) kernels.  Every body handles
-// the one particle p of the calling thread; keys_body and scatter_body use warp-wide votes and
-// must be called by all 32 lanes of a warp (live marks the lanes that own a particle).
+// shared by the single-box kernels and the multi-box (ensemble) kernels.  The binning bodies
+// (count_key, place_record and the four-particle keys_x4_body, scatter_x4_body) use warp-wide
+// votes and must be called by all 32 lanes of a warp (live marks the lanes that own a
+// particle); the gather and kick/drift bodies handle the one particle p of the calling thread.
 #pragma once
 #include "cola_internal.cuh"
 #include "pm_common.cuh"
@@ -37,20 +38,9 @@ __device__ __forceinline__ void count_key(int key, bool live, int* __restrict__ 
   if (live && lane == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
-// Bin key of particle p (plus bin_base) into keys[p]; counts[key] += 1 with one atomic per
-// distinct key in the warp.  s is the box's SoA [3][np^3] displacement.
-__device__ __forceinline__ void keys_body(const Geometry& g, const Tiles& tl, const float* __restrict__ s, int64_t p,
-                                          bool live, int bin_base, int* __restrict__ keys, int* __restrict__ counts,
-                                          int* __restrict__ err) {
-  int key = -1;
-  if (live) {
-    key = bin_base + particle_key(g, tl, p, s[p], s[g.np3 + p], s[2 * g.np3 + p], err);
-    keys[p] = key;
-  }
-  count_key(key, live, counts);
-}
-
-// Record of particle p: fixed-point CIC coordinates and lattice index (see scatter_body).
+// Record of particle p: its fixed-point CIC coordinates f_d = (cell << F) | t (each < ng 2^F <=
+// 2^31) and its lattice index, so the deposit and the gather read them in bin order with one
+// 16-byte access.
 __device__ __forceinline__ uint4 particle_record(const Geometry& g, int64_t p, float sx, float sy, float sz) {
   int ix, iy, iz;
   lattice_index(g, p, ix, iy, iz);
@@ -77,18 +67,6 @@ __device__ __forceinline__ void place_record(int key, bool live, uint4 r, int* _
   if (live && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
   base = __shfl_sync(peers, base, leader);
   if (live) rec[base + __popc(peers & ((1u << lane) - 1u))] = r;
-}
-
-// Counting-sort scatter: pos = cursor[keys[p]]++ (one atomic per distinct key in the warp) and
-// rec[pos] = (f_x, f_y, f_z, p): the particle's fixed-point CIC coordinates f_d = (cell << F) | t
-// (each < ng 2^F <= 2^31) and its lattice index, so the deposit and the gather read them in bin
-// order with one 16-byte access.
-__device__ __forceinline__ void scatter_body(const Geometry& g, const float* __restrict__ s, int64_t p, bool live,
-                                             const int* __restrict__ keys, int* __restrict__ cursor,
-                                             uint4* __restrict__ rec) {
-  const int key = live ? keys[p] : -1;
-  const uint4 r = live ? particle_record(g, p, s[p], s[g.np3 + p], s[2 * g.np3 + p]) : make_uint4(0, 0, 0, 0);
-  place_record(key, live, r, cursor, rec);
 }
 
 // Four particles per thread in warp-strided rounds: the block of nt threads takes the 4 nt
