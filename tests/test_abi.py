@@ -78,6 +78,12 @@ def test_calls_without_workspace_are_rejected(lib):
         rc = cdll.cola_step(h, 0, None, None, None, None, None)
         assert rc == 5  # COLA_ENOWORKSPACE
         assert b"workspace" in cdll.cola_last_error()
+        # every compute call checks for the workspace before it looks at its arguments
+        for call, args in (("cola_density_power", (h, None, 8, None, None, None, None)),
+                           ("cola_power", (h, None, 8, None, None, None, None)),
+                           ("cola_density", (h, None, None, None, None)),
+                           ("cola_force", (h, None, None, None))):
+            assert getattr(cdll, call)(*args) == 5, call
     finally:
         lib.cola_plan_destroy(h)
 
