@@ -1,10 +1,12 @@
 """Host-side bookkeeping of bench.py, on CPU: the algorithmic bytes it credits each force-evaluation
 kernel with against the DRAM bytes ncu measured for the same launches (the committed 1024^3 /
 2048^3 summary), the per-evaluation floor against those kernels, and the clock sampler's
-throttle-reason window."""
+throttle-reason window, and the bench commands the profile summaries give."""
+import glob
 import json
 import os
 import re
+import sys
 
 import bench
 
@@ -96,3 +98,18 @@ def test_clock_sampler_reads_reasons_inside_the_timed_window_only():
     cs.mark(10.0, 11.0)
     out = cs.stop()
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_profile_commands_run_committed_files_with_valid_bench_flags(monkeypatch):
+    # every bench command a profile summary was made with still parses, on a known workload
+    from paper_1301_0322_gb300 import inputs
+    n = 0
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        assert "_work" not in text, path
+        for m in re.finditer(r"python bench\.py([^\\`\n#]*)", text):
+            monkeypatch.setattr(sys, "argv", ["bench.py"] + m.group(1).split())
+            args = bench.parse_args()  # argparse exits on a flag bench.py does not take
+            assert args.workload in inputs.WORKLOADS, (path, args.workload)
+            n += 1
+    assert n > 0
