@@ -1,6 +1,6 @@
 """Host-side bookkeeping of bench.py, on CPU: the algorithmic bytes it credits each force-evaluation
 kernel with against the DRAM bytes ncu measured for the same launches (the committed 1024^3 /
-2048^3 summary), the per-evaluation floor against those kernels, and the clock sampler's
+2048^3 summary), the per-evaluation floor against those kernels, the clock sampler's
 throttle-reason window, and the bench commands the profile summaries give."""
 import glob
 import json
